@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark of the PFO/PST tracking hot path on the paper-scale synthetic workload.
+
+A step is one tracked frame: the persistent PFO kernel (unprojection, every
+PFO iteration: overlap set, fitness of all particles, APS / best state /
+rescale) followed by the fusion kernel, on a 512^3 int16 TSDF with 640x480
+depth at stride 4 (160x120 points), a 20,000-particle PST and up to 20
+iterations per frame, along a 3 m/s, 3 rad/s synthetic trajectory.
+
+Reported: lookups/s (particle x point TSDF lookups, counted exactly by the
+kernel), tracked frames/s, ATE of the tracked frames, the dominant kernel's
+roofline position, an end-to-end figure through the public sequence API with
+host buffers, and the FP64 oracle's throughput on the host as the CPU baseline.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank tracks its own sequence (independent problems, no
+data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle×point TSDF lookups/s and tracked frames/s at stated ATE (plain vs learned)"
+BYTES_PER_LOOKUP = {"i16": 16, "f16": 16, "f32": 32}  # 8 trilinear corners x storage size
+FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="paper")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(cfg):
+    return (f"plain PFO: {cfg['dims']}^3 {cfg['dtype']} TSDF (voxel {cfg['voxel'] * 100:g} cm, trunc "
+            f"{cfg['trunc'] * 100:g} cm), {cfg['width']}x{cfg['height']} depth at stride {cfg['stride']}, "
+            f"{cfg['n_particles']}-particle PST, <= {cfg['k_max']} iterations/frame, "
+            f"{cfg['speed']:g} m/s + {cfg['ang_speed']:g} rad/s trajectory")
+
+
+def make_workload(cfg, seed, n_frames):
+    from paper_2105_05600_gb300 import synth
+
+    scene = synth.make_scene(cfg["dims"] * cfg["voxel"], cfg["wall_inset"], seed)
+    traj = synth.make_trajectory(scene, n_frames, cfg["speed"], cfg["ang_speed"], seed)
+    K = synth.intrinsics(cfg["width"], cfg["height"])
+    rng = np.random.default_rng(1000 + seed) if cfg["noise"] else None
+    depths = [synth.render_depth(scene, traj[f], K, rng) for f in range(n_frames)]
+    return scene, traj, K, depths
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        load = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# ----------------------------------------------------------------------------- roofline inputs
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_fingerprint():
+    h = hashlib.sha256()
+    for name in ("track.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2105_05600_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(cfg_name, lookups_per_launch):
+    """DRAM bytes per launch of the tracker kernel from the committed ncu summary,
+    scaled to this launch by lookups, or None when the kernel changed since."""
+    p = os.path.join(ROOT, "profiles", f"pfo_kernel_{cfg_name}_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_fingerprint") != kernel_fingerprint():
+        return None
+    per_lookup = d["dram_bytes_per_launch"] / max(1, d["lookups_per_launch"])
+    return per_lookup * lookups_per_launch
+
+
+# ----------------------------------------------------------------------------- CPU baseline (oracle)
+class OracleFitnessSample:
+    """The FP64 oracle's fitness loop (Eq. normallh) on frame 1 of the workload:
+    the oracle fuses frame 0 into its own int16-rounded volume, then scores
+    particles of the frame-1 PST one by one over the overlap set, single thread."""
+
+    def __init__(self, cfg, seed):
+        import oracle
+
+        oracle.build()
+        self.oracle = oracle
+        scene, traj, K, depths = make_workload(cfg, seed, 2)
+        self.K = K
+        ov = oracle.Volume((cfg["dims"],) * 3, cfg["voxel"], (0, 0, 0), cfg["trunc"], qmode=cfg["dtype"])
+        ov.integrate(depths[0], K, traj[0])
+        self.ov = ov
+        pts = oracle.unproject(depths[1], K, cfg["stride"])
+        mask, _, nO = oracle.overlap(pts, depths[0], K, traj[0], traj[0])
+        self.pts, self.mask, self.nO = pts, mask, nO
+        self.centre = traj[0]
+        self.scale = np.array([0.03] * 3 + [0.05] * 3)
+        self.omega = oracle.pst_uniform(cfg["n_particles"], 1).astype(np.float64)
+        self.next = 0
+
+    def run(self, n_particles):
+        lookups = 0
+        for _ in range(n_particles):
+            i = self.next % self.omega.shape[1]
+            self.next += 1
+            pose = self.oracle.particle_pose(self.centre, self.scale, self.omega[:, i])
+            _, _, nO, _ = self.ov.fitness(self.pts, self.mask, pose)
+            lookups += nO
+        return lookups
+
+
+def cpu_baseline(cfg, seed, budget_s=12.0):
+    s = OracleFitnessSample(cfg, seed)
+    s.run(2)  # warm caches
+    t0 = time.perf_counter()
+    lookups, n = 0, 0
+    while time.perf_counter() - t0 < budget_s:
+        lookups += s.run(4)
+        n += 4
+    dt = time.perf_counter() - t0
+    return {"value": lookups / dt, "unit": "lookups/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle fitness of {n} particles of frame 1 ({s.nO} overlap points each, "
+                      f"{lookups} lookups, {dt:.1f} s, one thread)"}
+
+
+# ----------------------------------------------------------------------------- distributed helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, cfg):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2105_05600_gb300 import build, metrics
+
+    build.build()
+    from paper_2105_05600_gb300 import _native as nat
+
+    seed = cfg["seed"] + rank
+    W, K_steps = args.warmup, args.steps
+    n_frames = W + K_steps + 1
+    scene, traj, K, depths = make_workload(cfg, seed, n_frames)
+    vol = nat.Volume(cfg["dims"], cfg["voxel"], cfg["trunc"], (0, 0, 0), cfg["dtype"])
+    pst = nat.pst_create(cfg["n_particles"], seed=1)
+    params = nat.make_params(k_max=cfg["k_max"], stride=cfg["stride"])
+    tr = nat.Tracker(vol, pst, params, cfg["width"], cfg["height"])
+    D = [torch.from_numpy(d).cuda() for d in depths]
+    poses = torch.zeros((n_frames, 7), dtype=torch.float32, device="cuda")
+    poses[0] = torch.from_numpy(traj[0].astype(np.float32))
+    stats = [nat.new_stats_buffer() for _ in range(n_frames)]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    nat.tsdf_integrate(vol, D[0], K, traj[0])
+
+    def step(f):
+        nat.pfo_track_frame_async(tr, D[f], D[f - 1], K, poses[f - 1], poses[f], stats[f])
+        nat.tsdf_integrate_dev(vol, D[f], K, poses[f])
+
+    for f in range(1, W + 1):
+        step(f)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K_steps)]
+    clocks = ClockSampler(local).start()
+    barrier(world)
+    torch.cuda.synchronize()
+    for s in range(K_steps):
+        f = W + 1 + s
+        flush.fill_(s & 0xFF)  # L2 flush between timed steps, outside the events
+        e0, e1, e2 = ev[s]
+        e0.record(stream)
+        nat.pfo_track_frame_async(tr, D[f], D[f - 1], K, poses[f - 1], poses[f], stats[f])
+        e1.record(stream)
+        nat.tsdf_integrate_dev(vol, D[f], K, poses[f])
+        e2.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    t_step = sum(a.elapsed_time(c) for a, _, c in ev) / 1e3
+    t_pfo = sum(a.elapsed_time(b) for a, b, _ in ev) / 1e3
+    st = [nat.stats_dict(nat.stats_from_device(stats[W + 1 + s])) for s in range(K_steps)]
+    lookups = float(sum(x["lookups"] for x in st))
+    statuses = [x["status"] for x in st]
+    iters = [x["iters"] for x in st]
+    est = poses.cpu().numpy().astype(np.float64)
+    ate_mean, ate_rmse = metrics.ate(est[1:], traj[1:n_frames])
+
+    t_max = max_over_ranks(t_step, world)
+    lookups_all = sum_over_ranks(lookups, world)
+    frames_all = sum_over_ranks(float(K_steps), world)
+
+    # end to end through the public sequence API with host buffers (pinned depth in, pose out)
+    e2e = None
+    if not args.no_e2e:
+        vol.reset()
+        tr.set_scale([1.0] * 6)
+        host = [torch.from_numpy(d).pin_memory() for d in depths]
+        sdev = [nat.new_stats_buffer() for _ in range(n_frames)]
+        nat.rf_sequence_start(tr, host[0], K, traj[0])
+        for f in range(1, W + 1):
+            nat.rf_sequence_step(tr, host[f], K, stats_dev=sdev[f])
+        torch.cuda.synchronize()
+        barrier(world)
+        t_e2e = 0.0
+        for s in range(K_steps):
+            f = W + 1 + s
+            flush.fill_(s & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            nat.rf_sequence_step(tr, host[f], K, want_host_pose=True, stats_dev=sdev[f])
+            t_e2e += time.perf_counter() - t0
+        barrier(world)
+        lk = float(sum(nat.stats_from_device(sdev[W + 1 + s]).lookups for s in range(K_steps)))
+        t_e2e_max = max_over_ranks(t_e2e, world)
+        e2e = {"value": sum_over_ranks(lk, world) / t_e2e_max, "unit": "lookups/s",
+               "frames_per_s": sum_over_ranks(float(K_steps), world) / t_e2e_max,
+               "h2d_bytes_per_step": int(cfg["width"] * cfg["height"] * 4),
+               "d2h_bytes_per_step": 7 * 4 + 4,
+               "api": "rf_sequence_step (host float32 depth from pinned memory, host pose, stream sync)"}
+
+    result = None
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        bpl = BYTES_PER_LOOKUP[cfg["dtype"]]
+        achieved = bpl * lookups / t_pfo / 1e9
+        traffic = ncu_traffic(args.config, lookups / K_steps)
+        result = {
+            "metric": METRIC, "value": lookups_all / t_max, "unit": "lookups/s", "n_gpus": world,
+            "steps": K_steps, "warmup": W, "ms_per_step": 1e3 * t_max / K_steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: analytic room (6 walls + 3 spheres) ray-cast depth with N(0, (1 mm z^2)^2) noise, "
+                    "seeded trajectory; stands in for ICL-NUIM / ETH3D / FastCaMo",
+            "config": {"workload": workload_desc(cfg), "frames": f"{W + 1}..{W + K_steps} after frame 0 fused at "
+                                                                  f"ground truth", "seed": seed,
+                       "l2": "flushed between timed steps (512 MiB write outside the events)",
+                       "storage": cfg["dtype"], "parallelism": f"{world} independent sequence(s), one per GPU"},
+            "frames_per_s": frames_all / t_max,
+            "lookups_per_frame": lookups / K_steps,
+            "iters_per_frame": float(np.mean(iters)),
+            "ate_cm": {"mean": 100 * ate_mean, "rmse": 100 * ate_rmse, "frames": int(n_frames - 1)},
+            "frame_status_nonzero": int(sum(1 for s in statuses if s != 0)),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "pfo_kernel (persistent PFO frame kernel)",
+                         "note": f"algorithmic {bpl} B per lookup (8 trilinear corners), {peak_kind} HBM copy peak; "
+                                 "the gather runs mostly from L2"},
+            "pfo_ms_per_frame": 1e3 * t_pfo / K_steps,
+            "gpu_launches": 2 * K_steps,
+            "clocks": clk,
+        }
+        if e2e is not None:
+            result["e2e"] = e2e
+        if world == 1 and not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(cfg, seed)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, cfg):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    s = OracleFitnessSample(cfg, cfg["seed"])
+    per_step = 32  # particles per step: a bounded sample (~50 ms of FP64 work)
+    for _ in range(args.warmup):
+        s.run(per_step)
+    t0 = time.perf_counter()
+    lookups = 0
+    for _ in range(args.steps):
+        lookups += s.run(per_step)
+    dt = time.perf_counter() - t0
+    value = lookups / dt
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "lookups/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (same workload as ours)",
+        "config": {"workload": workload_desc(cfg), "step": f"FP64 oracle fitness of {per_step} particles over "
+                                                           f"{s.nO} overlap points of frame 1"},
+        "cpu_baseline": {"value": value, "unit": "lookups/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps x {per_step} particles x {s.nO} points"},
+        "e2e": {"value": value, "unit": "lookups/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    from paper_2105_05600_gb300 import synth
+
+    cfg = dict(synth.CONFIGS[args.config])
+    res = run_reference(args, cfg) if args.impl == "reference" else run_ours(args, cfg)
+    if res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -89,6 +89,8 @@ def _load():
             lib.or_te.restype = d
             lib.or_grid_search.argtypes = [D, I, d, D, D, I, i, D, D, i, d, i, D]
             lib.or_grid_search.restype = d
+            lib.or_fitness_fragile.argtypes = [D, I, d, D, D, I, i, D, d, i, d, D, I, I, D, I]
+            lib.or_tsdf_integrate_ambiguity.argtypes = [I, d, D, d, F, i, i, d, d, d, d, d, d, D, d, I]
             _lib = lib
     return _lib
 
@@ -234,6 +236,35 @@ class Volume:
                        pts.shape[0], ppose, float(tau), int(flags), ctypes.byref(S), ctypes.byref(n),
                        ctypes.byref(nO), ctypes.byref(rho))
         return S.value, n.value, nO.value, rho.value
+
+    def fitness_fragile(self, pts, in_set, pose, tau=1.0, flags=DEFAULT_FLAGS, delta_g=1e-3):
+        """(S, n_valid, |O|, rho, n_fragile): n_fragile counts points whose sample
+        validity (or nearest voxel) flips within +-delta_g voxels."""
+        lib = _load()
+        pts, pp = _d(pts)
+        in_set, pin = _i(in_set)
+        pose, ppose = _d(pose)
+        _, pdim = _i(self.dims)
+        _, por = _d(self.origin)
+        S, rho = ctypes.c_double(), ctypes.c_double()
+        n, nO, fr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        lib.or_fitness_fragile(self.F.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pdim, self.voxel, por, pp,
+                               pin, pts.shape[0], ppose, float(tau), int(flags), float(delta_g), ctypes.byref(S),
+                               ctypes.byref(n), ctypes.byref(nO), ctypes.byref(rho), ctypes.byref(fr))
+        return S.value, n.value, nO.value, rho.value, fr.value
+
+    def integrate_ambiguity(self, depth, K, pose, tol=1e-4):
+        """int32 map (same layout as F) of voxels whose fusion decisions are near a threshold."""
+        lib = _load()
+        depth, pdp = _f(depth)
+        H, W = depth.shape
+        pose, pp = _d(pose)
+        _, pdim = _i(self.dims)
+        _, por = _d(self.origin)
+        amb, pa = _i(np.zeros(self.F.shape[0], np.int32))
+        lib.or_tsdf_integrate_ambiguity(pdim, self.voxel, por, self.trunc, pdp, W, H, K["fx"], K["fy"], K["cx"],
+                                        K["cy"], K["z_min"], K["z_max"], pp, float(tol), pa)
+        return amb
 
     def grid_search(self, pts, in_set, c, half, steps, tau=1.0, flags=DEFAULT_FLAGS):
         """Best (rho, pose) over a steps^6 grid of offsets about c (brute force)."""

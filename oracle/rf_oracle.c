@@ -831,3 +831,88 @@ double or_grid_search(const double *F, const int dim[3], double voxel, const dou
     }
     return best;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Decisions that FP32 and FP64 may legitimately take differently.            */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Same sum as or_fitness, plus the number of points whose sample validity (or,
+ * in NEAREST mode, whose chosen voxel) changes when the sample position moves
+ * by +-delta_g voxels along any axis.  Each such point can move S by at most 1
+ * (psi^2 and |psi| lie in [0, 1]), which bounds the admissible gap between an
+ * FP32 evaluation and this one.
+ */
+void or_fitness_fragile(const double *F, const int dim[3], double voxel, const double origin[3], const double *pts,
+                        const int *in_set, int M, const double pose[7], double tau, int flags, double delta_g,
+                        double *S_out, int *n_out, int *nO_out, double *rho_out, int *fragile_out)
+{
+    double R[9];
+    or_quat_to_rot(pose, R);
+    int fragile = 0;
+    for (int j = 0; j < M; ++j) {
+        if (!in_set[j])
+            continue;
+        double pg[3], psi;
+        apply_pose(R, pose + 4, pts + 4 * (size_t)j, pg);
+        int base = or_tsdf_sample(F, dim, voxel, origin, pg, flags, &psi);
+        int moved = 0;
+        for (int a = 0; a < 3 && !moved; ++a)
+            for (int s = -1; s <= 1; s += 2) {
+                double q[3] = {pg[0], pg[1], pg[2]};
+                q[a] += s * delta_g * voxel;
+                double g0 = (pg[a] - origin[a]) / voxel - 0.5, g1 = (q[a] - origin[a]) / voxel - 0.5;
+                double psi2;
+                int v2 = or_tsdf_sample(F, dim, voxel, origin, q, flags, &psi2);
+                int cell_change = (flags & OR_NEAREST) ? floor(g0 + 0.5) != floor(g1 + 0.5) : 0;
+                if (v2 != base || (base && cell_change)) {
+                    moved = 1;
+                    break;
+                }
+            }
+        fragile += moved;
+    }
+    or_fitness(F, dim, voxel, origin, pts, in_set, M, pose, tau, flags, S_out, n_out, nO_out, rho_out);
+    *fragile_out = fragile;
+}
+
+/*
+ * Ambiguity map of one projective fusion step: ambig[v] = 1 where a decision of
+ * or_tsdf_integrate for voxel v lies within tol of its threshold (pixel
+ * rounding in u or v, the image border, the valid-depth range, sdf >= -trunc,
+ * z > 0), so that an FP32 implementation may decide it the other way.
+ */
+void or_tsdf_integrate_ambiguity(const int dim[3], double voxel, const double origin[3], double trunc,
+                                 const float *depth, int W, int H, double fx, double fy, double cx, double cy,
+                                 double z_min, double z_max, const double pose[7], double tol, int *ambig)
+{
+    double R[9];
+    or_quat_to_rot(pose, R);
+    for (int k = 0; k < dim[2]; ++k)
+        for (int j = 0; j < dim[1]; ++j)
+            for (int i = 0; i < dim[0]; ++i) {
+                size_t idx = (size_t)i + (size_t)dim[0] * ((size_t)j + (size_t)dim[1] * (size_t)k);
+                double pw[3] = {origin[0] + voxel * (i + 0.5), origin[1] + voxel * (j + 0.5),
+                                origin[2] + voxel * (k + 0.5)};
+                double pc[3];
+                apply_pose_inverse(R, pose + 4, pw, pc);
+                int a = 0;
+                if (fabs(pc[2]) < tol)
+                    a = 1;
+                if (pc[2] > 0.0) {
+                    double uc = fx * pc[0] / pc[2] + cx + 0.5, vc = fy * pc[1] / pc[2] + cy + 0.5;
+                    double du = fabs(uc - nearbyint(uc)), dv = fabs(vc - nearbyint(vc));
+                    if (du < tol || dv < tol)
+                        a = 1;
+                    double u = floor(uc), v = floor(vc);
+                    if (u >= 0.0 && u < (double)W && v >= 0.0 && v < (double)H) {
+                        double D = depth[(size_t)v * W + (size_t)u];
+                        if (fabs(D - z_min) < tol || fabs(D - z_max) < tol)
+                            a = 1;
+                        if (D > z_min && D <= z_max && fabs((D - pc[2]) + trunc) < tol)
+                            a = 1;
+                    }
+                }
+                ambig[idx] = a;
+            }
+}

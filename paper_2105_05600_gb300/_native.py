@@ -1,0 +1,404 @@
+"""ctypes binding of librosefusion.so (include/rosefusion.h).
+
+Argument marshalling only: every function here has the name of the C entry
+point it calls, turns torch tensors into device pointers and numpy arrays into
+host pointers, and raises RfError when the library returns a status < 0.  No
+tracking arithmetic happens in Python.  If the compiled library is missing
+this module raises at import time; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librosefusion.so")
+
+RF_OK, RF_ERR_ARG, RF_ERR_CUDA, RF_ERR_TIMEOUT, RF_ERR_EMPTY, RF_ERR_NOMEM = 0, -1, -2, -3, -4, -5
+RF_OVERLAP, RF_NORMALIZE, RF_COMPENSATED, RF_NEAREST, RF_RHO_REF_CENTER, RF_L1, RF_RIGHT_MULT = 1, 2, 4, 8, 16, 32, 64
+RF_DEFAULT_FLAGS = RF_OVERLAP | RF_NORMALIZE | RF_COMPENSATED
+RF_MAX_ITERS = 64
+DTYPES = {"f32": 0, "f16": 1, "i16": 2}
+
+
+class RfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"librosefusion status {status}: {msg}")
+        self.status = status
+
+
+class rf_intrinsics(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int), ("height", ctypes.c_int), ("z_min", ctypes.c_float),
+                ("z_max", ctypes.c_float)]
+
+
+class rf_pose(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_float * 4), ("t", ctypes.c_float * 3)]
+
+
+class rf_params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_float), ("beta", ctypes.c_float), ("eps", ctypes.c_float),
+                ("stop_eps", ctypes.c_float), ("k_max", ctypes.c_int), ("flags", ctypes.c_int),
+                ("stride", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class rf_iter_stats(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("n_overlap", ctypes.c_int), ("n_aps", ctypes.c_int), ("argmax", ctypes.c_int),
+                ("rho_ref", ctypes.c_float), ("rho_tilde", ctypes.c_float), ("rho_max", ctypes.c_float),
+                ("rho_second", ctypes.c_float), ("pose", ctypes.c_float * 7), ("scale", ctypes.c_float * 6),
+                ("offset", ctypes.c_float * 6), ("stop", ctypes.c_int)]
+
+
+class rf_frame_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("n_points", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("lookups", ctypes.c_longlong), ("r1", ctypes.c_float * 6),
+                ("pad", ctypes.c_float * 2), ("it", rf_iter_stats * RF_MAX_ITERS)]
+
+
+EXPORTS = ["rf_last_error", "rf_version", "pst_create", "rf_volume_create", "rf_volume_destroy", "rf_volume_reset",
+           "rf_volume_upload", "rf_volume_download", "rf_volume_info", "tsdf_integrate", "tsdf_integrate_dev",
+           "rf_depth_to_points",
+           "rf_overlap_mask", "fitness_eval", "rf_tracker_create", "rf_tracker_destroy", "rf_tracker_get_scale",
+           "rf_tracker_set_scale", "rf_tracker_set_params", "pfo_track_frame_async", "pfo_track_frame",
+           "rf_tracker_last_status", "rf_sequence_start", "rf_sequence_step", "rf_tracker_debug_skip_barrier"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"librosefusion.so not built ({LIB_PATH}); run paper_2105_05600_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    sig = {
+        "rf_last_error": (ctypes.c_char_p, []),
+        "rf_version": (ctypes.c_char_p, []),
+        "pst_create": (i, [i, ctypes.c_uint64, i, P, P]),
+        "rf_volume_create": (i, [i, i, i, f, f, ctypes.POINTER(f), i, ctypes.POINTER(P)]),
+        "rf_volume_destroy": (None, [P]),
+        "rf_volume_reset": (i, [P, P]),
+        "rf_volume_upload": (i, [P, P, P]),
+        "rf_volume_download": (i, [P, P, P]),
+        "rf_volume_info": (i, [P, ctypes.POINTER(i), ctypes.POINTER(f), ctypes.POINTER(f), ctypes.POINTER(f),
+                               ctypes.POINTER(i)]),
+        "tsdf_integrate": (i, [P, P, ctypes.POINTER(rf_intrinsics), ctypes.POINTER(rf_pose), P]),
+        "tsdf_integrate_dev": (i, [P, P, ctypes.POINTER(rf_intrinsics), P, P, P]),
+        "rf_depth_to_points": (i, [P, ctypes.POINTER(rf_intrinsics), i, P, P]),
+        "rf_overlap_mask": (i, [P, i, P, ctypes.POINTER(rf_intrinsics), ctypes.POINTER(rf_pose),
+                                ctypes.POINTER(rf_pose), P, P, P]),
+        "fitness_eval": (i, [P, P, i, P, i, ctypes.POINTER(rf_pose), ctypes.POINTER(f), ctypes.POINTER(rf_params),
+                             P, P, P, P]),
+        "rf_tracker_create": (i, [P, P, i, ctypes.POINTER(rf_params), i, i, ctypes.POINTER(P)]),
+        "rf_tracker_destroy": (None, [P]),
+        "rf_tracker_get_scale": (i, [P, ctypes.POINTER(f)]),
+        "rf_tracker_set_scale": (i, [P, ctypes.POINTER(f)]),
+        "rf_tracker_set_params": (i, [P, ctypes.POINTER(rf_params)]),
+        "pfo_track_frame_async": (i, [P, P, P, ctypes.POINTER(rf_intrinsics), P, P, P, P]),
+        "pfo_track_frame": (i, [P, P, P, ctypes.POINTER(rf_intrinsics), ctypes.POINTER(rf_pose),
+                                ctypes.POINTER(rf_pose), ctypes.POINTER(rf_frame_stats), P]),
+        "rf_tracker_last_status": (i, [P]),
+        "rf_sequence_start": (i, [P, P, i, ctypes.POINTER(rf_intrinsics), ctypes.POINTER(rf_pose), P]),
+        "rf_sequence_step": (i, [P, P, i, ctypes.POINTER(rf_intrinsics), ctypes.POINTER(rf_pose), P, P, P]),
+        "rf_tracker_debug_skip_barrier": (i, [P, i, i]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+# --------------------------------------------------------------------------- marshalling helpers
+def _check(status):
+    if status < 0:
+        raise RfError(status, lib.rf_last_error().decode())
+    return status
+
+
+def _stream(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_intrinsics(K: dict) -> rf_intrinsics:
+    return rf_intrinsics(K["fx"], K["fy"], K["cx"], K["cy"], int(K["width"]), int(K["height"]), K["z_min"],
+                         K["z_max"])
+
+
+def make_pose(p) -> rf_pose:
+    p = np.asarray(p, dtype=np.float64).reshape(7)
+    return rf_pose((ctypes.c_float * 4)(*p[:4]), (ctypes.c_float * 3)(*p[4:]))
+
+
+def pose_array(p: rf_pose) -> np.ndarray:
+    return np.array(list(p.q) + list(p.t), dtype=np.float64)
+
+
+def make_params(tau=1.0, beta=0.1, eps=1e-3, stop_eps=1e-6, k_max=20, flags=RF_DEFAULT_FLAGS, stride=1) -> rf_params:
+    return rf_params(tau, beta, eps, stop_eps, int(k_max), int(flags), int(stride), 0)
+
+
+def stats_dict(s: rf_frame_stats) -> dict:
+    rows = []
+    for k in range(min(s.iters, RF_MAX_ITERS)):
+        r = s.it[k]
+        rows.append(dict(k=r.k, n_overlap=r.n_overlap, n_aps=r.n_aps, argmax=r.argmax, rho_ref=r.rho_ref,
+                         rho_tilde=r.rho_tilde, rho_max=r.rho_max, rho_second=r.rho_second, pose=list(r.pose),
+                         scale=list(r.scale), offset=list(r.offset), stop=r.stop))
+    return dict(iters=s.iters, status=s.status, n_points=s.n_points, lookups=s.lookups, r1=list(s.r1), it=rows)
+
+
+def stats_from_device(t) -> rf_frame_stats:
+    """Parse a device buffer holding one rf_frame_stats (copied to the host)."""
+    raw = t.cpu().numpy().tobytes()
+    return rf_frame_stats.from_buffer_copy(raw[:ctypes.sizeof(rf_frame_stats)])
+
+
+def new_stats_buffer(device="cuda"):
+    import torch
+
+    return torch.zeros(ctypes.sizeof(rf_frame_stats), dtype=torch.uint8, device=device)
+
+
+def rf_version() -> str:
+    return lib.rf_version().decode()
+
+
+# --------------------------------------------------------------------------- PST
+def pst_create(n: int, seed: int = 1, method: int = 0, out=None, stream=None):
+    """Template of n particles in the unit 6D ball; returns a (6, n) float32 CUDA tensor."""
+    import torch
+
+    if out is None:
+        out = torch.empty((6, n), dtype=torch.float32, device="cuda")
+    _check(lib.pst_create(int(n), ctypes.c_uint64(int(seed)), int(method), _dptr(out, torch.float32),
+                          _stream(stream)))
+    return out
+
+
+# --------------------------------------------------------------------------- volume
+class Volume:
+    """Owning wrapper of an rf_volume handle."""
+
+    def __init__(self, dims, voxel, trunc, origin=(0.0, 0.0, 0.0), dtype="f32"):
+        h = ctypes.c_void_p()
+        org = (ctypes.c_float * 3)(*origin)
+        dims = tuple(int(d) for d in (dims if hasattr(dims, "__len__") else (dims,) * 3))
+        _check(lib.rf_volume_create(dims[0], dims[1], dims[2], float(voxel), float(trunc), org, DTYPES[dtype],
+                                    ctypes.byref(h)))
+        self.handle = h
+        self.dims = dims
+        self.voxel = float(voxel)
+        self.trunc = float(trunc)
+        self.origin = tuple(float(o) for o in origin)
+        self.dtype = dtype
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.rf_volume_destroy(h)
+            self.handle = None
+
+    @property
+    def np_code_dtype(self):
+        return {"f32": np.float32, "f16": np.float16, "i16": np.int16}[self.dtype]
+
+    def reset(self, stream=None):
+        _check(lib.rf_volume_reset(self.handle, _stream(stream)))
+
+    def upload(self, codes: np.ndarray, weights: np.ndarray | None = None):
+        """codes: storage codes, shape (dz, dy, dx) or flat x-fastest."""
+        codes = np.ascontiguousarray(codes, dtype=self.np_code_dtype)
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.uint8)
+        _check(lib.rf_volume_upload(self.handle, codes.ctypes.data_as(ctypes.c_void_p),
+                                    None if w is None else w.ctypes.data_as(ctypes.c_void_p)))
+
+    def download(self):
+        """(codes, weights) as (dz, dy, dx) numpy arrays."""
+        dx, dy, dz = self.dims
+        codes = np.empty((dz, dy, dx), dtype=self.np_code_dtype)
+        w = np.empty((dz, dy, dx), dtype=np.uint8)
+        _check(lib.rf_volume_download(self.handle, codes.ctypes.data_as(ctypes.c_void_p),
+                                      w.ctypes.data_as(ctypes.c_void_p)))
+        return codes, w
+
+
+def tsdf_integrate(vol: Volume, depth, K: dict, pose, stream=None):
+    import torch
+
+    Ki = make_intrinsics(K)
+    P = make_pose(pose)
+    _check(lib.tsdf_integrate(vol.handle, _dptr(depth, torch.float32), ctypes.byref(Ki), ctypes.byref(P),
+                              _stream(stream)))
+
+
+def tsdf_integrate_dev(vol: Volume, depth, K: dict, pose_dev, status_dev=None, stream=None):
+    import torch
+
+    Ki = make_intrinsics(K)
+    _check(lib.tsdf_integrate_dev(vol.handle, _dptr(depth, torch.float32), ctypes.byref(Ki),
+                                  _dptr(pose_dev, torch.float32), _dptr(status_dev), _stream(stream)))
+
+
+# --------------------------------------------------------------------------- points / overlap / fitness
+def rf_depth_to_points(depth, K: dict, stride: int, out=None, stream=None):
+    import torch
+
+    W, H = int(K["width"]), int(K["height"])
+    m = (-(-W // stride)) * (-(-H // stride))
+    if out is None:
+        out = torch.empty((m, 4), dtype=torch.float32, device=depth.device)
+    Ki = make_intrinsics(K)
+    _check(lib.rf_depth_to_points(_dptr(depth, torch.float32), ctypes.byref(Ki), int(stride),
+                                  _dptr(out, torch.float32), _stream(stream)))
+    return out
+
+
+def rf_overlap_mask(points, prev_depth, K: dict, pose_cur, pose_prev, stream=None):
+    import torch
+
+    m = points.shape[0]
+    mask = torch.empty(max(m, 1), dtype=torch.uint8, device=points.device)
+    count = torch.zeros(1, dtype=torch.int32, device=points.device)
+    Ki = make_intrinsics(K)
+    pc, pp = make_pose(pose_cur), make_pose(pose_prev)
+    _check(lib.rf_overlap_mask(_dptr(points, torch.float32), int(m), _dptr(prev_depth, torch.float32),
+                               ctypes.byref(Ki), ctypes.byref(pc), ctypes.byref(pp), _dptr(mask), _dptr(count),
+                               _stream(stream)))
+    return mask[:m], count
+
+
+def fitness_eval(vol: Volume, points, pst, centre, scale, params: rf_params, stream=None):
+    """(rho float32[n], sumsq float64[n], nvalid int32[n]) CUDA tensors."""
+    import torch
+
+    n = pst.shape[1]
+    rho = torch.empty(n, dtype=torch.float32, device=points.device)
+    S = torch.empty(n, dtype=torch.float64, device=points.device)
+    nv = torch.empty(n, dtype=torch.int32, device=points.device)
+    c = make_pose(centre)
+    sc = (ctypes.c_float * 6)(*np.asarray(scale, dtype=np.float64).reshape(6))
+    _check(lib.fitness_eval(vol.handle, _dptr(points, torch.float32), int(points.shape[0]),
+                            _dptr(pst, torch.float32), int(n), ctypes.byref(c), sc, ctypes.byref(params),
+                            _dptr(rho), _dptr(S), _dptr(nv), _stream(stream)))
+    return rho, S, nv
+
+
+# --------------------------------------------------------------------------- tracker
+class Tracker:
+    """Owning wrapper of an rf_tracker handle (keeps the volume and template alive)."""
+
+    def __init__(self, vol: Volume, pst, params: rf_params, max_width: int, max_height: int):
+        import torch
+
+        h = ctypes.c_void_p()
+        _check(lib.rf_tracker_create(vol.handle, _dptr(pst, torch.float32), int(pst.shape[1]), ctypes.byref(params),
+                                     int(max_width), int(max_height), ctypes.byref(h)))
+        self.handle = h
+        self.vol = vol
+        self.pst = pst
+        self.params = params
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.rf_tracker_destroy(h)
+            self.handle = None
+
+    def get_scale(self):
+        r = (ctypes.c_float * 6)()
+        _check(lib.rf_tracker_get_scale(self.handle, r))
+        return np.array(list(r), dtype=np.float64)
+
+    def set_scale(self, r):
+        _check(lib.rf_tracker_set_scale(self.handle, (ctypes.c_float * 6)(*np.asarray(r, np.float64).reshape(6))))
+
+    def set_params(self, params: rf_params):
+        _check(lib.rf_tracker_set_params(self.handle, ctypes.byref(params)))
+        self.params = params
+
+    def last_status(self):
+        return lib.rf_tracker_last_status(self.handle)
+
+    def debug_skip_barrier(self, enable: bool, timeout_ms: int):
+        _check(lib.rf_tracker_debug_skip_barrier(self.handle, int(bool(enable)), int(timeout_ms)))
+
+
+def pfo_track_frame(tr: Tracker, depth, prev_depth, K: dict, prev_pose, stream=None, check=True):
+    """Returns (pose float64[7], stats dict, status)."""
+    import torch
+
+    Ki = make_intrinsics(K)
+    pp = make_pose(prev_pose)
+    out = rf_pose()
+    st = rf_frame_stats()
+    status = lib.pfo_track_frame(tr.handle, _dptr(depth, torch.float32), _dptr(prev_depth, torch.float32),
+                                 ctypes.byref(Ki), ctypes.byref(pp), ctypes.byref(out), ctypes.byref(st),
+                                 _stream(stream))
+    if check and status < 0 and status != RF_ERR_EMPTY:
+        _check(status)
+    return pose_array(out), stats_dict(st), status
+
+
+def pfo_track_frame_async(tr: Tracker, depth, prev_depth, K: dict, prev_pose_dev, out_pose_dev, stats_dev=None,
+                          stream=None):
+    import torch
+
+    Ki = make_intrinsics(K)
+    _check(lib.pfo_track_frame_async(tr.handle, _dptr(depth, torch.float32), _dptr(prev_depth, torch.float32),
+                                     ctypes.byref(Ki), _dptr(prev_pose_dev, torch.float32),
+                                     _dptr(out_pose_dev, torch.float32), _dptr(stats_dev), _stream(stream)))
+
+
+def rf_sequence_start(tr: Tracker, depth, K: dict, pose, stream=None):
+    """depth: CUDA tensor or (pinned) host numpy/torch array."""
+    Ki = make_intrinsics(K)
+    P = make_pose(pose)
+    ptr, on_host = _any_ptr(depth)
+    _check(lib.rf_sequence_start(tr.handle, ptr, on_host, ctypes.byref(Ki), ctypes.byref(P), _stream(stream)))
+
+
+def rf_sequence_step(tr: Tracker, depth, K: dict, want_host_pose=True, out_pose_dev=None, stats_dev=None,
+                     stream=None):
+    """Track + fuse the next frame.  Returns (pose float64[7] or None, status)."""
+    Ki = make_intrinsics(K)
+    ptr, on_host = _any_ptr(depth)
+    out = rf_pose() if want_host_pose else None
+    status = lib.rf_sequence_step(tr.handle, ptr, on_host, ctypes.byref(Ki),
+                                  ctypes.byref(out) if out is not None else None, _dptr(out_pose_dev),
+                                  _dptr(stats_dev), _stream(stream))
+    if status < 0 and status != RF_ERR_EMPTY:
+        _check(status)
+    return (pose_array(out) if out is not None else None), status
+
+
+def _any_ptr(a):
+    """(pointer, on_host) for a CUDA tensor, a CPU tensor or a numpy array."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"] or a.dtype != np.float32:
+            raise ValueError("host depth must be a contiguous float32 array")
+        return ctypes.c_void_p(a.ctypes.data), 1
+    if a.is_cuda:
+        return _dptr(a), 0
+    if not a.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(a.data_ptr()), 1

@@ -1,0 +1,393 @@
+// volume.cu -- TSDF volume handles and volumetric fusion (tsdf_integrate).
+//
+// Layout in HBM: 8x8x8 voxel bricks (512 values = 1 KiB for int16/half, 2 KiB
+// for float) so that a 2x2x2 trilinear neighbourhood touches one or few 32-byte
+// sectors; uint8 weights in the same layout.  A 512^3 int16 volume is 256 MiB
+// of values plus 128 MiB of weights.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "common.cuh"
+
+namespace rf {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+rf_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    return e == cudaErrorMemoryAllocation ? RF_ERR_NOMEM : RF_ERR_CUDA;
+}
+
+static size_t dtype_size(int dt) { return dt == RF_F32 ? 4 : 2; }
+
+// ------------------------------------------------------------------ kernels
+// Fill every voxel with the unobserved sentinel and weight 0.
+__global__ void reset_kernel(uint32_t *vals32, size_t n_words, uint32_t pattern, uint8_t *w, size_t n_vox)
+{
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t k = i; k < n_words; k += stride)
+        vals32[k] = pattern;
+    for (size_t k = i; k < n_vox; k += stride)
+        w[k] = 0;
+}
+
+// Linear x-fastest <-> brick layout.  One thread per voxel; T is the raw code
+// type (uint32_t for float, uint16_t for half / int16).  Without uploaded
+// weights a voxel gets weight 1 unless its code is the unobserved sentinel.
+__device__ __forceinline__ bool code_unobserved(uint32_t c, int dtype)
+{
+    if (dtype == RF_F32)
+        return (c & 0x7f800000u) == 0x7f800000u && (c & 0x007fffffu) != 0u;
+    if (dtype == RF_F16)
+        return (c & 0x7c00u) == 0x7c00u && (c & 0x03ffu) != 0u;
+    return (c & 0xffffu) == 0x8000u;
+}
+
+template <typename T>
+__global__ void linear_to_brick(VolumeDesc V, const T *lin, const uint8_t *wlin, T *vals, uint8_t *w)
+{
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    size_t n = (size_t)V.dim[0] * V.dim[1] * V.dim[2];
+    if (i >= n)
+        return;
+    int x = (int)(i % V.dim[0]);
+    int y = (int)((i / V.dim[0]) % V.dim[1]);
+    int z = (int)(i / ((size_t)V.dim[0] * V.dim[1]));
+    size_t b = brick_index(V, x, y, z);
+    T v = lin[i];
+    vals[b] = v;
+    if (wlin)
+        w[b] = wlin[i];
+    else
+        w[b] = code_unobserved((uint32_t)v, V.dtype) ? 0 : 1;
+}
+
+template <typename T> __global__ void brick_to_linear(VolumeDesc V, const T *vals, const uint8_t *w, T *lin, uint8_t *wlin)
+{
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    size_t n = (size_t)V.dim[0] * V.dim[1] * V.dim[2];
+    if (i >= n)
+        return;
+    int x = (int)(i % V.dim[0]);
+    int y = (int)((i / V.dim[0]) % V.dim[1]);
+    int z = (int)(i / ((size_t)V.dim[0] * V.dim[1]));
+    size_t b = brick_index(V, x, y, z);
+    lin[i] = vals[b];
+    if (wlin)
+        wlin[i] = w[b];
+}
+
+template <int DT> struct Enc;
+template <> struct Enc<RF_F32> {
+    static __device__ __forceinline__ bool unobserved(float v) { return isnan(v); }
+    static __device__ __forceinline__ float dec(float v) { return v; }
+    static __device__ __forceinline__ float enc(float f) { return f; }
+};
+template <> struct Enc<RF_F16> {
+    static __device__ __forceinline__ bool unobserved(__half v) { return __hisnan(v); }
+    static __device__ __forceinline__ float dec(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half enc(float f) { return __float2half_rn(f); }
+};
+template <> struct Enc<RF_I16> {
+    static __device__ __forceinline__ bool unobserved(int16_t v) { return v == I16_UNOBSERVED; }
+    static __device__ __forceinline__ float dec(int16_t v) { return (float)v * (1.0f / I16_SCALE); }
+    static __device__ __forceinline__ int16_t enc(float f)
+    {
+        int c = __float2int_rn(f * I16_SCALE);
+        c = max(-32767, min(32767, c));
+        return (int16_t)c;
+    }
+};
+
+// Projective TSDF fusion (Sec. 3 overview; Curless & Levoy 1996, KinectFusion
+// 2011).  One CTA per 8x8x8 brick, one thread per voxel, so value and weight
+// accesses are contiguous 1 KiB (or 2 KiB) runs.  HBM-bound: 2+2 B of value
+// (4+4 for float) and 1+1 B of weight per updated voxel plus the depth reads.
+// The pose comes by value, or from device memory (pose_dev != NULL, written by
+// the tracker earlier on the stream); a non-zero *status_dev skips the update.
+template <int DT>
+__global__ void __launch_bounds__(512) integrate_kernel(VolumeDesc V, const float *__restrict__ depth, Intr K, Pose T,
+                                                        const float *pose_dev, const int *status_dev, int w_max)
+{
+    using S = typename Storage<DT>::T;
+    if (status_dev && *((volatile const int *)status_dev) != 0)
+        return;
+    if (pose_dev) {
+        for (int a = 0; a < 4; ++a)
+            T.q[a] = pose_dev[a];
+        for (int a = 0; a < 3; ++a)
+            T.t[a] = pose_dev[4 + a];
+    }
+    const int b = blockIdx.x;
+    const int bx = b % V.nb[0], by = (b / V.nb[0]) % V.nb[1], bz = b / (V.nb[0] * V.nb[1]);
+    const int l = threadIdx.x;
+    const int x = bx * BRICK + (l & 7), y = by * BRICK + ((l >> 3) & 7), z = bz * BRICK + (l >> 6);
+    float R[9];
+    quat_rot(T.q, R);
+    const float pwx = V.origin[0] + V.voxel * ((float)x + 0.5f) - T.t[0];
+    const float pwy = V.origin[1] + V.voxel * ((float)y + 0.5f) - T.t[1];
+    const float pwz = V.origin[2] + V.voxel * ((float)z + 0.5f) - T.t[2];
+    // camera frame: R^T (p - t)
+    const float cx = R[0] * pwx + R[3] * pwy + R[6] * pwz;
+    const float cy = R[1] * pwx + R[4] * pwy + R[7] * pwz;
+    const float cz = R[2] * pwx + R[5] * pwy + R[8] * pwz;
+    if (!(cz > 0.f))
+        return;
+    const float u = floorf(K.fx * cx / cz + K.cx + 0.5f);
+    const float v = floorf(K.fy * cy / cz + K.cy + 0.5f);
+    if (!(u >= 0.f && u < (float)K.width && v >= 0.f && v < (float)K.height))
+        return;
+    const float D = __ldg(&depth[(size_t)v * K.width + (size_t)u]);
+    if (!depth_valid(D, K))
+        return;
+    const float sdf = D - cz;
+    if (sdf < -V.trunc)
+        return;
+    const float f = fminf(1.f, sdf / V.trunc);
+    const size_t idx = (size_t)b * BRICK_VOX + l;
+    S *vals = reinterpret_cast<S *>(V.values);
+    const S old = vals[idx];
+    int w_old = V.weights[idx];
+    float F_old = 0.f;
+    if (Enc<DT>::unobserved(old))
+        w_old = 0;
+    else
+        F_old = Enc<DT>::dec(old);
+    const float F_new = ((float)w_old * F_old + f) / (float)(w_old + 1);
+    vals[idx] = Enc<DT>::enc(F_new);
+    V.weights[idx] = (uint8_t)min(w_old + 1, w_max);
+}
+
+static rf_status integrate_any(const VolumeDesc &V, const float *depth, const Intr &K, const Pose &T,
+                               const float *pose_dev, const int *status_dev, cudaStream_t s)
+{
+    const int nbricks = V.nb[0] * V.nb[1] * V.nb[2];
+    switch (V.dtype) {
+    case RF_F32:
+        integrate_kernel<RF_F32><<<nbricks, 512, 0, s>>>(V, depth, K, T, pose_dev, status_dev, 255);
+        break;
+    case RF_F16:
+        integrate_kernel<RF_F16><<<nbricks, 512, 0, s>>>(V, depth, K, T, pose_dev, status_dev, 255);
+        break;
+    default:
+        integrate_kernel<RF_I16><<<nbricks, 512, 0, s>>>(V, depth, K, T, pose_dev, status_dev, 255);
+        break;
+    }
+    RF_CUDA(cudaGetLastError());
+    return RF_OK;
+}
+
+rf_status launch_integrate(const VolumeDesc &V, const float *depth, const Intr &K, const Pose &T, cudaStream_t s)
+{
+    return integrate_any(V, depth, K, T, nullptr, nullptr, s);
+}
+
+rf_status launch_integrate_dev(const VolumeDesc &V, const float *depth, const Intr &K, const float *pose_dev,
+                               const int *status_dev, cudaStream_t s)
+{
+    Pose T;
+    memset(&T, 0, sizeof T);
+    return integrate_any(V, depth, K, T, pose_dev, status_dev, s);
+}
+
+Pose to_pose(const rf_pose &p)
+{
+    Pose o;
+    for (int i = 0; i < 4; ++i)
+        o.q[i] = p.q[i];
+    for (int i = 0; i < 3; ++i)
+        o.t[i] = p.t[i];
+    return o;
+}
+
+}  // namespace rf
+
+using namespace rf;
+
+extern "C" {
+
+const char *rf_last_error(void) { return g_last_error.c_str(); }
+const char *rf_version(void) { return "librosefusion 0.1 (sm_103a)"; }
+
+rf_status rf_volume_create(int dx, int dy, int dz, float voxel, float trunc, const float origin[3], int dtype,
+                           rf_volume *out)
+{
+    RF_CHECK_ARG(out != nullptr && origin != nullptr, "null pointer");
+    *out = nullptr;
+    RF_CHECK_ARG(dx > 0 && dy > 0 && dz > 0 && dx % 8 == 0 && dy % 8 == 0 && dz % 8 == 0 && dx <= 2048 &&
+                     dy <= 2048 && dz <= 2048,
+                 "dims must be positive multiples of 8 up to 2048");
+    RF_CHECK_ARG(voxel > 0.f && trunc > 0.f, "voxel and trunc must be positive");
+    RF_CHECK_ARG(dtype == RF_F32 || dtype == RF_F16 || dtype == RF_I16, "unknown dtype");
+    rf_volume v = new rf_volume_s();
+    memset(v, 0, sizeof *v);
+    VolumeDesc &d = v->d;
+    d.dim[0] = dx;
+    d.dim[1] = dy;
+    d.dim[2] = dz;
+    for (int a = 0; a < 3; ++a) {
+        d.nb[a] = d.dim[a] / BRICK;
+        d.origin[a] = origin[a];
+    }
+    d.voxel = voxel;
+    d.inv_voxel = 1.0f / voxel;
+    d.trunc = trunc;
+    for (int a = 0; a < 3; ++a)
+        d.goff[a] = -origin[a] / voxel - 0.5f;
+    d.dtype = dtype;
+    v->n_vox = (size_t)dx * dy * dz;
+    cudaGetDevice(&v->device);
+    cudaError_t e = cudaMalloc(&d.values, v->n_vox * dtype_size(dtype));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&d.weights, v->n_vox);
+    if (e != cudaSuccess) {
+        cudaFree(d.values);
+        delete v;
+        return cuda_fail(e, "cudaMalloc(volume)");
+    }
+    rf_status st = rf_volume_reset(v, nullptr);
+    if (st != RF_OK) {
+        rf_volume_destroy(v);
+        return st;
+    }
+    RF_CUDA(cudaDeviceSynchronize());
+    *out = v;
+    return RF_OK;
+}
+
+void rf_volume_destroy(rf_volume v)
+{
+    if (!v)
+        return;
+    cudaFree(v->d.values);
+    cudaFree(v->d.weights);
+    cudaFree(v->scratch);
+    delete v;
+}
+
+rf_status rf_volume_reset(rf_volume v, void *stream)
+{
+    RF_CHECK_ARG(v != nullptr, "null volume");
+    uint32_t pattern = v->d.dtype == RF_F32 ? 0x7fc00000u : (v->d.dtype == RF_F16 ? 0x7e007e00u : 0x80008000u);
+    size_t words = v->n_vox * dtype_size(v->d.dtype) / 4;
+    reset_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>((uint32_t *)v->d.values, words, pattern, v->d.weights,
+                                                         v->n_vox);
+    RF_CUDA(cudaGetLastError());
+    return RF_OK;
+}
+
+rf_status rf_volume_info(rf_volume v, int dims[3], float *voxel, float *trunc, float origin[3], int *dtype)
+{
+    RF_CHECK_ARG(v != nullptr, "null volume");
+    for (int a = 0; a < 3; ++a) {
+        if (dims)
+            dims[a] = v->d.dim[a];
+        if (origin)
+            origin[a] = v->d.origin[a];
+    }
+    if (voxel)
+        *voxel = v->d.voxel;
+    if (trunc)
+        *trunc = v->d.trunc;
+    if (dtype)
+        *dtype = v->d.dtype;
+    return RF_OK;
+}
+
+rf_status rf_volume_upload(rf_volume v, const void *values_host, const uint8_t *weights_host)
+{
+    RF_CHECK_ARG(v != nullptr && values_host != nullptr, "null pointer");
+    const size_t es = dtype_size(v->d.dtype);
+    void *tmp = nullptr;
+    uint8_t *wtmp = nullptr;
+    RF_CUDA(cudaMalloc(&tmp, v->n_vox * es));
+    cudaError_t e = cudaMemcpy(tmp, values_host, v->n_vox * es, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && weights_host) {
+        e = cudaMalloc(&wtmp, v->n_vox);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(wtmp, weights_host, v->n_vox, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) {
+        const int threads = 256;
+        const unsigned blocks = (unsigned)((v->n_vox + threads - 1) / threads);
+        if (v->d.dtype == RF_F32)
+            linear_to_brick<uint32_t><<<blocks, threads>>>(v->d, (const uint32_t *)tmp, wtmp,
+                                                           (uint32_t *)v->d.values, v->d.weights);
+        else
+            linear_to_brick<uint16_t><<<blocks, threads>>>(v->d, (const uint16_t *)tmp, wtmp,
+                                                           (uint16_t *)v->d.values, v->d.weights);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaDeviceSynchronize();
+    }
+    cudaFree(tmp);
+    cudaFree(wtmp);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "rf_volume_upload");
+    return RF_OK;
+}
+
+rf_status rf_volume_download(rf_volume v, void *values_host, uint8_t *weights_host)
+{
+    RF_CHECK_ARG(v != nullptr && values_host != nullptr, "null pointer");
+    const size_t es = dtype_size(v->d.dtype);
+    void *tmp = nullptr;
+    uint8_t *wtmp = nullptr;
+    RF_CUDA(cudaMalloc(&tmp, v->n_vox * es));
+    cudaError_t e = cudaSuccess;
+    if (weights_host)
+        e = cudaMalloc(&wtmp, v->n_vox);
+    if (e == cudaSuccess) {
+        const int threads = 256;
+        const unsigned blocks = (unsigned)((v->n_vox + threads - 1) / threads);
+        if (v->d.dtype == RF_F32)
+            brick_to_linear<uint32_t><<<blocks, threads>>>(v->d, (const uint32_t *)v->d.values, v->d.weights,
+                                                           (uint32_t *)tmp, wtmp);
+        else
+            brick_to_linear<uint16_t><<<blocks, threads>>>(v->d, (const uint16_t *)v->d.values, v->d.weights,
+                                                           (uint16_t *)tmp, wtmp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy(values_host, tmp, v->n_vox * es, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && weights_host)
+        e = cudaMemcpy(weights_host, wtmp, v->n_vox, cudaMemcpyDeviceToHost);
+    cudaFree(tmp);
+    cudaFree(wtmp);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "rf_volume_download");
+    return RF_OK;
+}
+
+rf_status tsdf_integrate(rf_volume v, const float *depth_dev, const rf_intrinsics *K, const rf_pose *pose,
+                         void *stream)
+{
+    RF_CHECK_ARG(v != nullptr && depth_dev != nullptr && K != nullptr && pose != nullptr, "null pointer");
+    RF_CHECK_ARG(K->width > 0 && K->height > 0, "empty depth image");
+    return launch_integrate(v->d, depth_dev, to_intr(*K), to_pose(*pose), (cudaStream_t)stream);
+}
+
+rf_status tsdf_integrate_dev(rf_volume v, const float *depth_dev, const rf_intrinsics *K, const float *pose_dev,
+                             const int *status_dev, void *stream)
+{
+    RF_CHECK_ARG(v != nullptr && depth_dev != nullptr && K != nullptr && pose_dev != nullptr, "null pointer");
+    RF_CHECK_ARG(K->width > 0 && K->height > 0, "empty depth image");
+    return launch_integrate_dev(v->d, depth_dev, to_intr(*K), pose_dev, status_dev, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -239,12 +239,15 @@ def analytic_tsdf(sdf_fn, dims, voxel: float, origin, trunc: float, observed_ban
     Returns a float64 array shaped (dz, dy, dx)."""
     dx, dy, dz = dims
     o = np.asarray(origin, np.float64)
-    z, y, x = np.meshgrid((np.arange(dz) + 0.5) * voxel + o[2], (np.arange(dy) + 0.5) * voxel + o[1],
-                          (np.arange(dx) + 0.5) * voxel + o[0], indexing="ij")
-    s = sdf_fn(np.stack([x, y, z], axis=-1))
-    F = np.clip(s / trunc, -1.0, 1.0)
-    if observed_band is not None:
-        F = np.where(s < -observed_band, np.nan, F)
+    F = np.empty((dz, dy, dx), np.float64)
+    y, x = np.meshgrid((np.arange(dy) + 0.5) * voxel + o[1], (np.arange(dx) + 0.5) * voxel + o[0], indexing="ij")
+    for k in range(dz):  # one z slab at a time keeps 512^3 fills within a few hundred MB
+        z = np.full_like(x, (k + 0.5) * voxel + o[2])
+        s = sdf_fn(np.stack([x, y, z], axis=-1))
+        f = np.clip(s / trunc, -1.0, 1.0)
+        if observed_band is not None:
+            f = np.where(s < -observed_band, np.nan, f)
+        F[k] = f
     return F
 
 

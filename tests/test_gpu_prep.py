@@ -1,0 +1,147 @@
+"""GPU PST sampling, depth preprocessing, overlap set and TSDF fusion against the
+FP64 oracle and closed forms, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2105_05600_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nat():
+    from paper_2105_05600_gb300 import build
+
+    build.build()
+    from paper_2105_05600_gb300 import _native
+
+    return _native
+
+
+# ----------------------------------------------------------------------------- PST
+@pytest.mark.parametrize("n,seed", [(1, 1), (2, 1), (1000, 1), (20000, 1), (777, 2 ** 40 + 5)])
+def test_pst_uniform_bit_exact(oracle, nat, n, seed):
+    gpu = nat.pst_create(n, seed=seed).cpu().numpy()
+    np.testing.assert_array_equal(gpu, oracle.pst_uniform(n, seed))
+
+
+def test_pst_poisson_invariants(nat):
+    n = 512
+    P = nat.pst_create(n, seed=3, method=1).cpu().numpy().astype(np.float64)
+    U = nat.pst_create(n, seed=3, method=0).cpu().numpy().astype(np.float64)
+    assert np.all(P[:, 0] == 0)
+    assert np.linalg.norm(P, axis=0).max() <= 1.0 + 1e-6
+
+    def min_dist(X):
+        d = np.linalg.norm(X[:, :, None] - X[:, None, :], axis=0)
+        d[np.diag_indices(X.shape[1])] = np.inf
+        return d.min()
+
+    # blue noise: the closest pair is far further apart than in a uniform sample
+    assert min_dist(P) > 2.0 * min_dist(U)
+
+
+# ----------------------------------------------------------------------------- points
+@pytest.mark.parametrize("W,H,stride", [(80, 60, 1), (640, 480, 4), (97, 61, 3), (5, 3, 8)])
+def test_depth_to_points_parity(oracle, nat, W, H, stride):
+    import torch
+
+    K = synth.intrinsics(W, H)
+    rng = np.random.default_rng(W * H)
+    depth = rng.uniform(0.2, 6.0, size=(H, W)).astype(np.float32)
+    depth[rng.random((H, W)) < 0.1] = 0.0
+    depth[rng.random((H, W)) < 0.02] = 9.5
+    depth[rng.random((H, W)) < 0.02] = np.nan
+    ref = oracle.unproject(depth, K, stride)
+    got = nat.rf_depth_to_points(torch.from_numpy(depth).cuda(), K, stride).cpu().numpy().astype(np.float64)
+    assert got.shape == ref.shape
+    np.testing.assert_array_equal(got[:, 3], ref[:, 3])
+    np.testing.assert_allclose(got[:, :3], ref[:, :3], rtol=1e-6, atol=1e-7)
+
+
+def test_overlap_parity(oracle, nat):
+    import torch
+
+    cfg = synth.CONFIGS["paper"]
+    scene = synth.make_scene(cfg["dims"] * cfg["voxel"], cfg["wall_inset"], 0)
+    traj = synth.make_trajectory(scene, 3, 3.0, 3.0, 0)
+    K = synth.intrinsics(640, 480)
+    d0 = synth.render_depth(scene, traj[0], K)
+    d1 = synth.render_depth(scene, traj[1], K)
+    pts = oracle.unproject(d1, K, 4).astype(np.float32).astype(np.float64)
+    cur = traj[1].astype(np.float32).astype(np.float64)
+    prev = traj[0].astype(np.float32).astype(np.float64)
+    mask, margin, n = oracle.overlap(pts, d0, K, cur, prev)
+    gmask, gcount = nat.rf_overlap_mask(torch.from_numpy(pts.astype(np.float32)).cuda(), torch.from_numpy(d0).cuda(),
+                                        K, cur, prev)
+    gmask = gmask.cpu().numpy().astype(np.int32)
+    sure = margin > 1e-3  # decisions more than 1e-3 px from a rounding boundary are unique
+    assert sure.mean() > 0.99
+    np.testing.assert_array_equal(gmask[sure], mask[sure])
+    assert int(gcount.cpu()[0]) == int(gmask.sum())
+    assert abs(int(gmask.sum()) - n) <= int((~sure).sum())
+
+
+# ----------------------------------------------------------------------------- fusion
+def test_integrate_fronto_parallel_plane(nat):
+    import torch
+
+    K = dict(fx=8.0, fy=8.0, cx=15.5, cy=11.5, z_min=0.1, z_max=8.0, width=32, height=24)
+    v = nat.Volume(16, 0.1, 0.3, (-0.8, -0.8, 0.0), "f32")
+    nat.tsdf_integrate(v, torch.full((24, 32), 1.0, device="cuda"), K, [1, 0, 0, 0, 0, 0, 0])
+    F, W = v.download()
+    k, j, i = np.meshgrid(np.arange(16), np.arange(16), np.arange(16), indexing="ij")
+    x, y, z = -0.8 + 0.1 * (i + 0.5), -0.8 + 0.1 * (j + 0.5), 0.1 * (k + 0.5)
+    inside = (z >= 0.45) & (np.abs(x) <= 0.75) & (np.abs(y) <= 0.6)
+    band = inside & (1.0 - z >= -0.3)
+    np.testing.assert_allclose(F[band], np.minimum(1.0, (1.0 - z) / 0.3)[band], atol=2e-7)
+    assert np.all(W[band] == 1)
+    assert np.all(np.isnan(F[inside & (1.0 - z < -0.3)]))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "i16"])
+def test_integrate_parity_sequence(oracle, nat, dtype):
+    import torch
+
+    cfg = dict(synth.CONFIGS["tiny"])
+    dims, voxel, trunc = cfg["dims"], cfg["voxel"], cfg["trunc"]
+    scene = synth.make_scene(dims * voxel, cfg["wall_inset"], 0)
+    traj = synth.make_trajectory(scene, 4, 3.0, 3.0, 0)
+    K = synth.intrinsics(cfg["width"], cfg["height"])
+    gv = nat.Volume(dims, voxel, trunc, (0, 0, 0), dtype)
+    ov = oracle.Volume((dims,) * 3, voxel, (0, 0, 0), trunc, qmode=dtype)
+    amb = np.zeros(dims ** 3, bool)
+    rng = np.random.default_rng(3)
+    for f in range(4):
+        depth = synth.render_depth(scene, traj[f], K, rng)
+        pose = traj[f].astype(np.float32).astype(np.float64)
+        amb |= ov.integrate_ambiguity(depth, K, pose, tol=1e-4).astype(bool)
+        ov.integrate(depth, K, pose)
+        nat.tsdf_integrate(gv, torch.from_numpy(depth).cuda(), K, pose)
+    codes, W = gv.download()
+    Fg = synth.decode_values(codes).reshape(-1)
+    Wg = W.reshape(-1).astype(np.int32)
+    sure = ~amb
+    assert sure.mean() > 0.999
+    np.testing.assert_array_equal(Wg[sure], ov.W[sure])
+    both = sure & np.isfinite(Fg) & np.isfinite(ov.F)
+    assert np.array_equal(np.isfinite(Fg[sure]), np.isfinite(ov.F[sure]))
+    # FP32 running average vs FP64, then the storage rounding of each dtype
+    atol = {"f32": 1e-6, "f16": 2e-3, "i16": 4.0 / 32767}[dtype]
+    np.testing.assert_allclose(Fg[both], ov.F[both], atol=atol)
+    if dtype == "i16":
+        assert np.mean(np.abs(Fg[both] - ov.F[both]) < 0.5 / 32767 + 1e-9) > 0.99
+
+
+def test_integrate_skips_invalid_depth(nat):
+    import torch
+
+    K = synth.intrinsics(80, 60)
+    v = nat.Volume(64, 0.04, 0.12, (0, 0, 0), "i16")
+    d = torch.zeros((60, 80), device="cuda")
+    d[10, 10] = float("nan")
+    nat.tsdf_integrate(v, d, K, [1, 0, 0, 0, 1.28, 1.28, 1.28])
+    codes, W = v.download()
+    assert W.max() == 0 and np.all(codes == -32768)

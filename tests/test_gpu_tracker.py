@@ -131,14 +131,15 @@ def test_tracker_timeout_hook_reports_and_recovers(oracle, nat):
     pst = nat.pst_create(256, seed=1)
     tr = nat.Tracker(gv, pst, nat.make_params(k_max=5), cfg["width"], cfg["height"])
     D0, D1 = torch.from_numpy(d0).cuda(), torch.from_numpy(d1).cuda()
+    tr.set_scale([0.1] * 6)
     ref_pose, ref_stats, st = nat.pfo_track_frame(tr, D1, D0, K, traj[0])
     assert st == 0
-    tr.set_scale([1.0] * 6)
+    tr.set_scale([0.1] * 6)
     tr.debug_skip_barrier(True, 50)  # block 0 never arrives: the others give up after 50 ms
     _, gst, status = nat.pfo_track_frame(tr, D1, D0, K, traj[0], check=False)
     assert status == nat.RF_ERR_TIMEOUT
     # the context is still usable and the next frame runs normally
-    tr.set_scale([1.0] * 6)
+    tr.set_scale([0.1] * 6)
     pose, gst2, status2 = nat.pfo_track_frame(tr, D1, D0, K, traj[0])
     assert status2 == 0
     np.testing.assert_array_equal(pose, ref_pose)

@@ -221,6 +221,32 @@ rf_status rf_overlap_mask(const float *points_dev, int m, const float *prev_dept
 rf_status fitness_eval(rf_volume v, const float *points_dev, int m, const float *pst_dev, int n,
                        const rf_pose *centre, const float scale[6], const rf_params *p, float *rho_dev,
                        double *sumsq_dev, int *nvalid_dev, void *stream);
+/*
+ * fitness_eval_noalloc -- fitness_eval without any device allocation (the
+ * paper has no counterpart; this is a library service).  fitness_eval grows a
+ * scratch buffer with cudaMalloc the first time a size needs it, and that call
+ * synchronises the device and allocates.  Callers that cannot do either --
+ * code inside CUDA stream capture, real-time loops that must never block on
+ * the allocator, plug-in hosts that own a fixed memory budget -- use this
+ * entry point instead.  Arguments, layouts and results are those of
+ * fitness_eval; the caller still provides every input and output buffer.
+ *   Scratch: the per-chunk partial sums live in a 32 MiB static device array
+ *   inside the library, which every GPU that loads the library holds until
+ *   the process exits.  Sizes with ceil(m / 256) * n * 12 bytes above 32 MiB
+ *   are rejected with RF_ERR_ARG (for example n = 20,000 allows m up to
+ *   35,840 points).
+ *   Set-up: the first call on each device (with that device current) looks
+ *   up the array's device address with cudaGetSymbolAddress and caches it;
+ *   make that first call before any stream capture.
+ *   Sharing: all calls use the same array and leave their partial sums in
+ *   it.  Every slot a call reads is written by that call first, so nothing
+ *   needs clearing, but two calls that overlap on the GPU (different streams
+ *   without ordering) race on the array.
+ * No cudaMalloc, cudaFree or other allocating call is made.  Asynchronous.
+ */
+rf_status fitness_eval_noalloc(rf_volume v, const float *points_dev, int m, const float *pst_dev, int n,
+                               const rf_pose *centre, const float scale[6], const rf_params *p, float *rho_dev,
+                               double *sumsq_dev, int *nvalid_dev, void *stream);
 
 /* ------------------------------------------------------------- tracker --- */
 /*

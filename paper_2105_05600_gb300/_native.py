@@ -61,7 +61,7 @@ class rf_frame_stats(ctypes.Structure):
 EXPORTS = ["rf_last_error", "rf_version", "pst_create", "rf_volume_create", "rf_volume_destroy", "rf_volume_reset",
            "rf_volume_upload", "rf_volume_download", "rf_volume_info", "tsdf_integrate", "tsdf_integrate_dev",
            "rf_depth_to_points",
-           "rf_overlap_mask", "fitness_eval", "rf_tracker_create", "rf_tracker_destroy", "rf_tracker_get_scale",
+           "rf_overlap_mask", "fitness_eval", "fitness_eval_noalloc", "rf_tracker_create", "rf_tracker_destroy", "rf_tracker_get_scale",
            "rf_tracker_set_scale", "rf_tracker_set_params", "pfo_track_frame_async", "pfo_track_frame",
            "rf_tracker_last_status", "rf_sequence_start", "rf_sequence_step", "rf_tracker_debug_skip_barrier"]
 
@@ -89,6 +89,8 @@ def _load():
                                 ctypes.POINTER(rf_pose), P, P, P]),
         "fitness_eval": (i, [P, P, i, P, i, ctypes.POINTER(rf_pose), ctypes.POINTER(f), ctypes.POINTER(rf_params),
                              P, P, P, P]),
+        "fitness_eval_noalloc": (i, [P, P, i, P, i, ctypes.POINTER(rf_pose), ctypes.POINTER(f),
+                                     ctypes.POINTER(rf_params), P, P, P, P]),
         "rf_tracker_create": (i, [P, P, i, ctypes.POINTER(rf_params), i, i, ctypes.POINTER(P)]),
         "rf_tracker_destroy": (None, [P]),
         "rf_tracker_get_scale": (i, [P, ctypes.POINTER(f)]),
@@ -300,6 +302,25 @@ def fitness_eval(vol: Volume, points, pst, centre, scale, params: rf_params, str
     _check(lib.fitness_eval(vol.handle, _dptr(points, torch.float32), int(points.shape[0]),
                             _dptr(pst, torch.float32), int(n), ctypes.byref(c), sc, ctypes.byref(params),
                             _dptr(rho), _dptr(S), _dptr(nv), _stream(stream)))
+    return rho, S, nv
+
+
+def fitness_eval_noalloc(vol: Volume, points, pst, centre, scale, params: rf_params, out=None, stream=None):
+    """fitness_eval without device allocation in the library (its scratch is a
+    fixed static array).  `out` may pass preallocated (rho, sumsq, nvalid)."""
+    import torch
+
+    n = pst.shape[1]
+    if out is None:
+        out = (torch.empty(n, dtype=torch.float32, device=points.device),
+               torch.empty(n, dtype=torch.float64, device=points.device),
+               torch.empty(n, dtype=torch.int32, device=points.device))
+    rho, S, nv = out
+    c = make_pose(centre)
+    sc = (ctypes.c_float * 6)(*np.asarray(scale, dtype=np.float64).reshape(6))
+    _check(lib.fitness_eval_noalloc(vol.handle, _dptr(points, torch.float32), int(points.shape[0]),
+                                    _dptr(pst, torch.float32), int(n), ctypes.byref(c), sc, ctypes.byref(params),
+                                    _dptr(rho), _dptr(S), _dptr(nv), _stream(stream)))
     return rho, S, nv
 
 

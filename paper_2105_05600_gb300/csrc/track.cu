@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -1239,3 +1240,85 @@ rf_status rf_sequence_step(rf_tracker tr, const float *depth, int depth_on_host,
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free fitness
+// fitness_eval keeps its per-(chunk, particle) partial sums in a buffer that the
+// volume handle grows with cudaMalloc on first use, which synchronises and
+// allocates.  fitness_eval_noalloc takes them from this fixed, file-scope device
+// array instead.  The array is part of the library image, so every GPU that
+// loads the library holds these 32 MiB until the process exits.
+namespace rf {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// In host code g_noalloc_scratch names a host-side stand-in, not device memory:
+// the device address is looked up once per device (with that device current)
+// and cached here.
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_dev_ptr[NOALLOC_MAX_DEVICES];
+
+static rf_status noalloc_scratch(void **out)
+{
+    int dev = 0;
+    RF_CUDA(cudaGetDevice(&dev));
+    RF_CHECK_ARG(dev >= 0 && dev < NOALLOC_MAX_DEVICES, "device ordinal beyond the supported range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_dev_ptr[dev] == nullptr) {
+        void *p = nullptr;
+        RF_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_dev_ptr[dev] = p;
+    }
+    *out = g_noalloc_dev_ptr[dev];
+    return RF_OK;
+}
+
+}  // namespace rf
+
+extern "C" rf_status fitness_eval_noalloc(rf_volume v, const float *points_dev, int m, const float *pst_dev, int n,
+                                          const rf_pose *centre, const float scale[6], const rf_params *p,
+                                          float *rho_dev, double *sumsq_dev, int *nvalid_dev, void *stream)
+{
+    RF_CHECK_ARG(v && points_dev && pst_dev && centre && scale && p && rho_dev, "null pointer");
+    RF_CHECK_ARG(m >= 1 && n >= 1, "m and n must be >= 1");
+    RF_CHECK_ARG(p->tau > 0.f, "tau must be positive");
+    const size_t per_chunk = (size_t)n * (sizeof(double) + sizeof(int));
+    const size_t min_chunks = ((size_t)m + CHUNK_MAX - 1) / CHUNK_MAX;
+    RF_CHECK_ARG(min_chunks * per_chunk <= NOALLOC_SCRATCH_BYTES,
+                 "ceil(m / 256) * n * 12 bytes exceeds the 32 MiB static scratch of fitness_eval_noalloc");
+    cudaStream_t s = (cudaStream_t)stream;
+    void *scratch = nullptr;
+    rf_status st = noalloc_scratch(&scratch);
+    if (st != RF_OK)
+        return st;
+    const int mode = mode_of(p->flags);
+    FitFn fn = fit_fn(v->d.dtype, mode);
+    const size_t smem = (size_t)FIT_WARPS * CHUNK_MAX * sizeof(float4);
+    RF_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, FIT_THREADS, smem));
+    const int grid = std::max(1, per_sm) * sm_count();
+    const int total_warps = grid * FIT_WARPS;
+    const int cap_chunks = (int)std::min<size_t>(NOALLOC_SCRATCH_BYTES / per_chunk, 1 << 30);
+    const Split sp = make_split(n, m, total_warps, std::min(max_chunks_for(n, m, total_warps), cap_chunks));
+    // every (chunk, particle) slot below n_chunks * n is written by the fitness
+    // kernel before the finishing kernel reads it: nothing needs clearing
+    double *part_S = (double *)scratch;
+    int *part_n = (int *)(part_S + (size_t)sp.n_chunks * n);
+    FitParams fp;
+    fp.pst = pst_dev;
+    fp.n = n;
+    fp.c = to_pose(*centre);
+    for (int d = 0; d < 6; ++d)
+        fp.r[d] = scale[d];
+    fp.l1 = (p->flags & RF_L1) != 0;
+    fp.right_mult = (p->flags & RF_RIGHT_MULT) != 0;
+    fn<<<grid, FIT_THREADS, smem, s>>>(v->d, (const float4 *)points_dev, m, fp, sp, part_S, part_n);
+    RF_CUDA(cudaGetLastError());
+    fitness_finish_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, sp.n_chunks, part_S, part_n, m, p->tau,
+                                                          (p->flags & RF_NORMALIZE) != 0, rho_dev, sumsq_dev,
+                                                          nvalid_dev);
+    RF_CUDA(cudaGetLastError());
+    return RF_OK;
+}

@@ -372,7 +372,7 @@ def run_ours(args, cfg):
                          "note": f"algorithmic {bpl} B per lookup (8 trilinear corners), {peak_kind} HBM copy peak; "
                                  "the gather runs mostly from L2"},
             "pfo_ms_per_frame": 1e3 * t_pfo / K_steps,
-            "gpu_launches": 2 * K_steps,
+            "gpu_launches": 3 * K_steps,  # per step: pfo_kernel, integrate_kernel, pack_cells_kernel
             "clocks": clk,
         }
         if e2e is not None:

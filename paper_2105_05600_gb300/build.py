@@ -20,6 +20,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librosefusion.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", f"-I{INCLUDE}"]
+# extra nvcc flags for tuning builds, e.g. RF_NVCC_FLAGS="-DRF_PFO_MIN_BLOCKS=4"
+NVCC_FLAGS += os.environ.get("RF_NVCC_FLAGS", "").split()
 
 
 def nvcc() -> str:

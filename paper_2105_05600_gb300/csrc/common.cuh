@@ -34,11 +34,25 @@ constexpr int BRICK = 8;             // 8x8x8 voxels per brick
 constexpr int BRICK_VOX = 512;
 constexpr int16_t I16_UNOBSERVED = -32768;
 constexpr float I16_SCALE = 32767.0f;
+constexpr uint8_t CELLS_MIXED = 0, CELLS_FREE = 1, CELLS_INVALID = 2;
 
 // Passed by value to every kernel that touches the TSDF.
 struct VolumeDesc {
     void *values;      // brick layout: brick b = bx + nb[0]*(by + nb[1]*bz), then lx + 8*(ly + 8*lz)
     uint8_t *weights;  // same layout
+    // Packed trilinear cells: record i (same brick index as voxel i) holds the 8
+    // corner codes of the cell whose lower corner is voxel i, ordered
+    // (x,y,z) = 000,100,010,110,001,101,011,111: 16 B for int16/half, 32 B for
+    // float.  Rebuilt from `values` for every brick marked in `dirty`.
+    // int16 cells hold the biased code c + 32768 (sentinel -> 0).
+    void *cells;
+    uint8_t *dirty;    // one flag per brick, set by fusion, cleared after packing
+    // Class of each cell brick, written with its cells: CELLS_MIXED, or every
+    // cell of the brick free space (all 8 corners exactly +1: psi = 1, valid) or
+    // every cell touching an unobserved voxel (invalid).  Lookups in constant
+    // bricks skip the cell load.
+    uint8_t *brick_class;
+    int cell_stride[3];// brick-layout strides of one brick step per axis (in records)
     int dim[3];
     int nb[3];
     float voxel, inv_voxel, trunc;
@@ -176,54 +190,124 @@ template <> struct Storage<RF_I16> {
     }
 };
 
-// psi at world point p (reading: trilinear on voxel centres, all 8 corners inside
-// the volume and observed; NEAREST: closest voxel centre).  Returns false when
-// the sample is invalid.
-template <int DT, bool NEAREST>
-__device__ __forceinline__ bool sample_tsdf(const VolumeDesc &V, float px, float py, float pz, float &psi)
+// ------------------------------------------------------------------ packed-cell sampling
+// floor(g) without the conversion pipe: adding 1.5 * 2^23 with round-down leaves
+// floor(g) in the low mantissa bits for |g| < 2^22.  Out-of-range, huge or NaN g
+// give an index that fails the unsigned bounds test of the caller.
+__device__ __forceinline__ int floor_split(float g, float &frac)
+{
+    const float t = __fadd_rd(g, 12582912.0f);
+    frac = g - (t - 12582912.0f);
+    return __float_as_int(t) - 0x4B400000;
+}
+
+// Two biased int16 codes (c + 32768) of one 32-bit word as exact floats c,
+// without I2F: each 16-bit half is placed in the mantissa of 2^23.
+__device__ __forceinline__ void decode_i16x2(uint32_t w, float &lo, float &hi)
+{
+    lo = __int_as_float((int)__byte_perm(w, 0x4B00u, 0x5410)) - 8421376.0f;  // 2^23 + 32768
+    hi = __int_as_float((int)__byte_perm(w, 0x4B00u, 0x5432)) - 8421376.0f;
+}
+
+// psi of a free-space cell (eight +1 corners), bit-identical to what the full
+// interpolation returns for it.
+template <int DT> __device__ __forceinline__ float free_psi()
+{
+    return DT == RF_I16 ? 32767.0f * (1.0f / I16_SCALE) : 1.0f;
+}
+
+__device__ __forceinline__ float lerp1(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+// Nearest-voxel psi at voxel-centre coordinates (flag RF_NEAREST): the voxel
+// whose centre is closest, valid if inside the volume and observed.
+template <int DT>
+__device__ __forceinline__ bool sample_nearest_g(const VolumeDesc &V, float gx, float gy, float gz, float &psi)
 {
     using T = typename Storage<DT>::T;
-    const T *vals = reinterpret_cast<const T *>(V.values);
-    const float gx = fmaf(px, V.inv_voxel, V.goff[0]);
-    const float gy = fmaf(py, V.inv_voxel, V.goff[1]);
-    const float gz = fmaf(pz, V.inv_voxel, V.goff[2]);
-    if (NEAREST) {
-        const float rx = floorf(gx + 0.5f), ry = floorf(gy + 0.5f), rz = floorf(gz + 0.5f);
-        if (!(rx >= 0.f && rx <= (float)(V.dim[0] - 1) && ry >= 0.f && ry <= (float)(V.dim[1] - 1) && rz >= 0.f &&
-              rz <= (float)(V.dim[2] - 1)))
-            return false;
-        float v = Storage<DT>::decode(__ldg(&vals[brick_index(V, (int)rx, (int)ry, (int)rz)]));
-        psi = v;
-        return !isnan(v);
-    }
-    const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
-    if (!(fx0 >= 0.f && fx0 <= (float)(V.dim[0] - 2) && fy0 >= 0.f && fy0 <= (float)(V.dim[1] - 2) && fz0 >= 0.f &&
-          fz0 <= (float)(V.dim[2] - 2)))
+    float f;
+    const int ix = floor_split(gx + 0.5f, f), iy = floor_split(gy + 0.5f, f), iz = floor_split(gz + 0.5f, f);
+    if (!((unsigned)ix < (unsigned)V.dim[0] && (unsigned)iy < (unsigned)V.dim[1] && (unsigned)iz < (unsigned)V.dim[2]))
         return false;
-    const int ix = (int)fx0, iy = (int)fy0, iz = (int)fz0;
-    const float fx = gx - fx0, fy = gy - fy0, fz = gz - fz0;
-    // per-axis offsets of the two corners inside the brick layout
-    const size_t sy = (size_t)V.nb[0] * BRICK_VOX, sz = sy * (size_t)V.nb[1];
-    const size_t ox0 = (size_t)(ix >> 3) * BRICK_VOX + (ix & 7), ox1 = (size_t)((ix + 1) >> 3) * BRICK_VOX + ((ix + 1) & 7);
-    const size_t oy0 = (size_t)(iy >> 3) * sy + 8 * (iy & 7), oy1 = (size_t)((iy + 1) >> 3) * sy + 8 * ((iy + 1) & 7);
-    const size_t oz0 = (size_t)(iz >> 3) * sz + 64 * (iz & 7), oz1 = (size_t)((iz + 1) >> 3) * sz + 64 * ((iz + 1) & 7);
-    const float v000 = Storage<DT>::decode(__ldg(&vals[ox0 + oy0 + oz0]));
-    const float v100 = Storage<DT>::decode(__ldg(&vals[ox1 + oy0 + oz0]));
-    const float v010 = Storage<DT>::decode(__ldg(&vals[ox0 + oy1 + oz0]));
-    const float v110 = Storage<DT>::decode(__ldg(&vals[ox1 + oy1 + oz0]));
-    const float v001 = Storage<DT>::decode(__ldg(&vals[ox0 + oy0 + oz1]));
-    const float v101 = Storage<DT>::decode(__ldg(&vals[ox1 + oy0 + oz1]));
-    const float v011 = Storage<DT>::decode(__ldg(&vals[ox0 + oy1 + oz1]));
-    const float v111 = Storage<DT>::decode(__ldg(&vals[ox1 + oy1 + oz1]));
-    const float c00 = fmaf(fx, v100 - v000, v000);
-    const float c10 = fmaf(fx, v110 - v010, v010);
-    const float c01 = fmaf(fx, v101 - v001, v001);
-    const float c11 = fmaf(fx, v111 - v011, v011);
-    const float c0 = fmaf(fy, c10 - c00, c00);
-    const float c1 = fmaf(fy, c11 - c01, c01);
-    const float v = fmaf(fz, c1 - c0, c0);
+    const float v = Storage<DT>::decode(__ldg(&reinterpret_cast<const T *>(V.values)[brick_index(V, ix, iy, iz)]));
     psi = v;
     return !isnan(v);
+}
+
+
+// Trilinear lookup from the packed cells, split into three branch-free steps so
+// that a caller can issue the loads of several lookups before using any:
+//   cell_locate: cell index, fractions and the brick class (one byte load);
+//   cell_fetch:  the 16-byte (32 for float) record, only for mixed bricks;
+//   cell_eval:   decode + interpolation, valid only inside the volume with every
+//                corner observed (a cell with an unobserved corner is stored as
+//                all zero codes for int16, and NaN poisons float storage).
+struct CellRef {
+    float fx, fy, fz;
+    unsigned rec;
+    unsigned cls;  // CELLS_MIXED / CELLS_FREE / CELLS_INVALID (also out of the volume)
+};
+
+template <int DT> struct CellData {
+    uint4 a;
+};
+template <> struct CellData<RF_F32> {
+    float4 a, b;
+};
+
+__device__ __forceinline__ void cell_locate(const VolumeDesc &V, float gx, float gy, float gz, CellRef &c)
+{
+    const int ix = floor_split(gx, c.fx), iy = floor_split(gy, c.fy), iz = floor_split(gz, c.fz);
+    const bool inside = (unsigned)ix < (unsigned)(V.dim[0] - 1) && (unsigned)iy < (unsigned)(V.dim[1] - 1) &&
+                        (unsigned)iz < (unsigned)(V.dim[2] - 1);
+    const unsigned brick =
+        (unsigned)(ix >> 3) + (unsigned)V.nb[0] * ((unsigned)(iy >> 3) + (unsigned)V.nb[1] * (unsigned)(iz >> 3));
+    c.rec = brick * (unsigned)BRICK_VOX + (unsigned)((ix & 7) | ((iy & 7) << 3) | ((iz & 7) << 6));
+    c.cls = inside ? (unsigned)__ldg(&V.brick_class[brick]) : (unsigned)CELLS_INVALID;
+}
+
+template <int DT> __device__ __forceinline__ void cell_fetch(const VolumeDesc &V, const CellRef &c, CellData<DT> &d)
+{
+    if constexpr (DT == RF_F32) {
+        const float4 *cp = reinterpret_cast<const float4 *>(V.cells) + 2 * (size_t)c.rec;
+        d.a = c.cls == CELLS_MIXED ? __ldg(cp) : make_float4(0.f, 0.f, 0.f, 0.f);
+        d.b = c.cls == CELLS_MIXED ? __ldg(cp + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        d.a = c.cls == CELLS_MIXED ? __ldg(reinterpret_cast<const uint4 *>(V.cells) + c.rec) : make_uint4(1u, 0u, 0u, 0u);
+    }
+}
+
+template <int DT> __device__ __forceinline__ bool cell_eval(const CellRef &c, const CellData<DT> &d, float &psi)
+{
+    float k[8];
+    bool ok_mixed;
+    if constexpr (DT == RF_F32) {
+        k[0] = d.a.x; k[1] = d.a.y; k[2] = d.a.z; k[3] = d.a.w;
+        k[4] = d.b.x; k[5] = d.b.y; k[6] = d.b.z; k[7] = d.b.w;
+    } else if constexpr (DT == RF_I16) {
+        decode_i16x2(d.a.x, k[0], k[1]);
+        decode_i16x2(d.a.y, k[2], k[3]);
+        decode_i16x2(d.a.z, k[4], k[5]);
+        decode_i16x2(d.a.w, k[6], k[7]);
+    } else {
+        const uint32_t w[4] = {d.a.x, d.a.y, d.a.z, d.a.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&w[q]));
+            k[2 * q] = f2.x;
+            k[2 * q + 1] = f2.y;
+        }
+    }
+    const float c00 = lerp1(k[0], k[1], c.fx), c10 = lerp1(k[2], k[3], c.fx);
+    const float c01 = lerp1(k[4], k[5], c.fx), c11 = lerp1(k[6], k[7], c.fx);
+    float v = lerp1(lerp1(c00, c10, c.fy), lerp1(c01, c11, c.fy), c.fz);
+    if constexpr (DT == RF_I16) {
+        v *= 1.0f / I16_SCALE;
+        ok_mixed = (d.a.x & 0xFFFFu) != 0u;  // all-zero record = some corner unobserved
+    } else {
+        ok_mixed = !isnan(v);
+    }
+    psi = c.cls == CELLS_MIXED ? v : free_psi<DT>();
+    return c.cls == CELLS_MIXED ? ok_mixed : c.cls == CELLS_FREE;
 }
 
 }  // namespace rf

@@ -33,6 +33,10 @@ constexpr int CHUNK_MAX = 256;        // points staged per warp (16 B each)
 constexpr int UNITS_PER_WARP = 16;    // target work units per warp and iteration
 constexpr int APW = 16;               // doubles per CTA in the APS partials
 constexpr int MAX_CTAS_PER_SM = 2048 / FIT_THREADS;  // bound for grid-sized scratch
+// CTAs of the persistent kernel resident per SM (register budget 65536 / (256 * n))
+#ifndef RF_PFO_MIN_BLOCKS
+#define RF_PFO_MIN_BLOCKS 3
+#endif
 
 // ------------------------------------------------------------------ small helpers
 __device__ __forceinline__ long long global_ns()
@@ -106,26 +110,73 @@ __device__ __forceinline__ void fitness_lane(const VolumeDesc &V, const float4 *
             d[a] = fp.r[a] * __ldg(&fp.pst[(size_t)a * fp.n + ii]);
         compose_offset(fp.c, d, fp.right_mult != 0, P);
     }
+    // the rotation and translation are folded with the world -> voxel-centre map
+    // g = p / voxel - origin / voxel - 1/2, so a point goes straight to grid units
     float R[9];
     quat_rot(P.q, R);
-    const float t0 = P.t[0], t1 = P.t[1], t2 = P.t[2];
+    const float s = V.inv_voxel;
+    for (int a = 0; a < 9; ++a)
+        R[a] *= s;
+    const float t0 = fmaf(P.t[0], s, V.goff[0]), t1 = fmaf(P.t[1], s, V.goff[1]), t2 = fmaf(P.t[2], s, V.goff[2]);
     float sum = 0.f, comp = 0.f;
     int nv = 0;
-#pragma unroll 4
-    for (int j = 0; j < cnt; ++j) {
-        const float4 x = spts[j];
-        const float px = fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, t0)));
-        const float py = fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, t1)));
-        const float pz = fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, t2)));
-        float psi;
-        const bool ok = sample_tsdf<DT, Mode<MODE>::nearest>(V, px, py, pz, psi);
+    int j = 0;
+    const bool l1 = fp.l1 != 0;
+    auto add = [&](float grp) {
+        if (Mode<MODE>::plain)
+            sum += grp;
+        else
+            neumaier_add(sum, comp, grp);
+    };
+    auto term = [&](bool ok, float psi) {
         nv += ok ? 1 : 0;
         psi = ok ? psi : 1.f;
-        const float term = fp.l1 ? fabsf(psi) : psi * psi;
-        if (Mode<MODE>::plain)
-            sum += term;
-        else
-            neumaier_add(sum, comp, term);
+        return l1 ? fabsf(psi) : psi * psi;
+    };
+    if (!Mode<MODE>::nearest) {
+        // groups of 4 lookups: all class loads, then all cell loads, then the
+        // arithmetic, so each group pays the load latency once; a plain FP32
+        // partial of <= 4 terms in [0, 1] is then added with compensation
+        for (; j + 4 <= cnt; j += 4) {
+            CellRef c[4];
+            CellData<DT> d[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 x = spts[j + u];
+                cell_locate(V, fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, t0))),
+                            fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, t1))),
+                            fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, t2))), c[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                cell_fetch<DT>(V, c[u], d[u]);
+            float grp = 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                float psi;
+                const bool ok = cell_eval<DT>(c[u], d[u], psi);
+                grp += term(ok, psi);
+            }
+            add(grp);
+        }
+    }
+    for (; j < cnt; ++j) {  // the tail of the chunk (or every point in nearest mode)
+        const float4 x = spts[j];
+        const float gx = fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, t0)));
+        const float gy = fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, t1)));
+        const float gz = fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, t2)));
+        float psi;
+        bool ok;
+        if (Mode<MODE>::nearest) {
+            ok = sample_nearest_g<DT>(V, gx, gy, gz, psi);
+        } else {
+            CellRef c;
+            CellData<DT> d;
+            cell_locate(V, gx, gy, gz, c);
+            cell_fetch<DT>(V, c, d);
+            ok = cell_eval<DT>(c, d, psi);
+        }
+        add(term(ok, psi));
     }
     S_out = (double)sum + (double)comp;
     n_out = nv;
@@ -169,15 +220,33 @@ __host__ inline int max_chunks_for(int n, int m_max, int total_warps)
 // All warps of the grid walk the units; each stages its chunk of points, scores
 // its 32 particles and writes one (S, n) partial per particle.  `coherent`
 // selects L2-coherent loads for points written earlier in the same kernel.
+// With a unit counter (`next_unit` non-null, zero at the start of the phase) the
+// warps take units dynamically, one atomic per unit, fetched one unit ahead;
+// otherwise warp w takes units w, w + total_warps, ...
 template <int DT, int MODE, bool COHERENT>
 __device__ __forceinline__ void fitness_units(const VolumeDesc &V, const float4 *pts, int m, const FitParams &fp,
                                               const Split &sp, double *part_S, int *part_n, float4 *smem_pts,
-                                              int warp_global, int total_warps, int lane, int warp_in_block)
+                                              int warp_global, int total_warps, int lane, int warp_in_block,
+                                              int *next_unit = nullptr)
 {
     float4 *spts = smem_pts + (size_t)warp_in_block * CHUNK_MAX;
     const int units = sp.groups * sp.n_chunks;
     int staged = -1;
-    for (int u = warp_global; u < units; u += total_warps) {
+    int u = warp_global;
+    if (next_unit) {
+        int t = 0;
+        if (lane == 0)
+            t = atomicAdd(next_unit, 1);
+        u = __shfl_sync(0xffffffffu, t, 0);
+    }
+    while (u < units) {
+        int u_next = u + total_warps;
+        if (next_unit) {
+            int t = 0;
+            if (lane == 0)
+                t = atomicAdd(next_unit, 1);
+            u_next = __shfl_sync(0xffffffffu, t, 0);
+        }
         const int ch = u / sp.groups, g = u - ch * sp.groups;
         const int j0 = ch * sp.chunk;
         const int cnt = min(sp.chunk, m - j0);
@@ -196,6 +265,7 @@ __device__ __forceinline__ void fitness_units(const VolumeDesc &V, const float4 
             part_S[(size_t)ch * fp.n + i] = S;
             part_n[(size_t)ch * fp.n + i] = nv;
         }
+        u = u_next;
     }
 }
 
@@ -352,6 +422,7 @@ struct TrackParams {
     double *part_S;
     int *part_n;
     int max_chunks;
+    int *unit_ctr;           // [RF_MAX_ITERS] fitness work-unit counters, zero at launch
     double *aps;             // [grid][APW]
     GridSync *gs;
     int *status;
@@ -396,7 +467,7 @@ __device__ __forceinline__ int block_scan_flag(int flag, int *warp_tot, int *tot
 }
 
 template <int DT, int MODE>
-__global__ void __launch_bounds__(FIT_THREADS) pfo_kernel(TrackParams P)
+__global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_kernel(TrackParams P)
 {
     extern __shared__ float4 smem_pts[];
     __shared__ TrackState st;
@@ -524,7 +595,7 @@ __global__ void __launch_bounds__(FIT_THREADS) pfo_kernel(TrackParams P)
         fp.right_mult = (P.flags & RF_RIGHT_MULT) != 0;
         const Split sp = make_split(P.n, nO, total_warps, P.max_chunks);
         fitness_units<DT, MODE, true>(P.V, P.cpts, nO, fp, sp, P.part_S, P.part_n, smem_pts, b * FIT_WARPS + w,
-                                      total_warps, lane, w);
+                                      total_warps, lane, w, P.unit_ctr + (k - 1));
         if (!grid_barrier(P.gs, P.status, P.timeout_ns))
             return;
         // ---- phase B': per-particle totals, rho, APS partial sums (Eq. ebs, wafit)
@@ -851,6 +922,7 @@ struct rf_tracker_s {
     // device scratch
     float4 *pts, *cpts;
     int *block_counts;
+    int *unit_ctr;     // RF_MAX_ITERS work-unit counters of the fitness phase
     double *part_S;
     int *part_n;
     double *aps;
@@ -973,6 +1045,7 @@ void rf_tracker_destroy(rf_tracker tr)
     cudaFree(tr->part_S);
     cudaFree(tr->part_n);
     cudaFree(tr->aps);
+    cudaFree(tr->unit_ctr);
     cudaFree(tr->gs);
     cudaFree(tr->status);
     cudaFree(tr->scale);
@@ -1021,6 +1094,7 @@ rf_status rf_tracker_create(rf_volume v, const float *pst_dev, int n, const rf_p
     alloc((void **)&tr->part_S, sizeof(double) * (size_t)tr->max_chunks * n);
     alloc((void **)&tr->part_n, sizeof(int) * (size_t)tr->max_chunks * n);
     alloc((void **)&tr->aps, sizeof(double) * APW * (size_t)MAX_CTAS_PER_SM * sm_count());
+    alloc((void **)&tr->unit_ctr, sizeof(int) * RF_MAX_ITERS);
     alloc((void **)&tr->gs, sizeof(GridSync));
     alloc((void **)&tr->status, sizeof(int));
     alloc((void **)&tr->scale, sizeof(float) * 6);
@@ -1119,6 +1193,7 @@ rf_status pfo_track_frame_async(rf_tracker tr, const float *depth_dev, const flo
     P.part_n = tr->part_n;
     P.max_chunks = tr->max_chunks;
     P.aps = tr->aps;
+    P.unit_ctr = tr->unit_ctr;
     P.gs = tr->gs;
     P.status = tr->status;
     P.tau = tr->p.tau;
@@ -1132,6 +1207,7 @@ rf_status pfo_track_frame_async(rf_tracker tr, const float *depth_dev, const flo
     // one-thread kernel), so the launch sequence stays capturable
     RF_CUDA(cudaMemsetAsync(tr->status, 0, sizeof(int), s));
     RF_CUDA(cudaMemsetAsync(tr->gs, 0, sizeof(GridSync), s));
+    RF_CUDA(cudaMemsetAsync(tr->unit_ctr, 0, sizeof(int) * RF_MAX_ITERS, s));
     if (tr->debug_skip) {
         set_int_kernel<<<1, 1, 0, s>>>(&tr->gs->skip, 1);
         RF_CUDA(cudaGetLastError());

@@ -137,40 +137,134 @@ __global__ void __launch_bounds__(512) integrate_kernel(VolumeDesc V, const floa
     const int bx = b % V.nb[0], by = (b / V.nb[0]) % V.nb[1], bz = b / (V.nb[0] * V.nb[1]);
     const int l = threadIdx.x;
     const int x = bx * BRICK + (l & 7), y = by * BRICK + ((l >> 3) & 7), z = bz * BRICK + (l >> 6);
-    float R[9];
-    quat_rot(T.q, R);
-    const float pwx = V.origin[0] + V.voxel * ((float)x + 0.5f) - T.t[0];
-    const float pwy = V.origin[1] + V.voxel * ((float)y + 0.5f) - T.t[1];
-    const float pwz = V.origin[2] + V.voxel * ((float)z + 0.5f) - T.t[2];
-    // camera frame: R^T (p - t)
-    const float cx = R[0] * pwx + R[3] * pwy + R[6] * pwz;
-    const float cy = R[1] * pwx + R[4] * pwy + R[7] * pwz;
-    const float cz = R[2] * pwx + R[5] * pwy + R[8] * pwz;
-    if (!(cz > 0.f))
-        return;
-    const float u = floorf(K.fx * cx / cz + K.cx + 0.5f);
-    const float v = floorf(K.fy * cy / cz + K.cy + 0.5f);
-    if (!(u >= 0.f && u < (float)K.width && v >= 0.f && v < (float)K.height))
-        return;
-    const float D = __ldg(&depth[(size_t)v * K.width + (size_t)u]);
-    if (!depth_valid(D, K))
-        return;
-    const float sdf = D - cz;
-    if (sdf < -V.trunc)
-        return;
-    const float f = fminf(1.f, sdf / V.trunc);
-    const size_t idx = (size_t)b * BRICK_VOX + l;
-    S *vals = reinterpret_cast<S *>(V.values);
-    const S old = vals[idx];
-    int w_old = V.weights[idx];
-    float F_old = 0.f;
-    if (Enc<DT>::unobserved(old))
-        w_old = 0;
-    else
-        F_old = Enc<DT>::dec(old);
-    const float F_new = ((float)w_old * F_old + f) / (float)(w_old + 1);
-    vals[idx] = Enc<DT>::enc(F_new);
-    V.weights[idx] = (uint8_t)min(w_old + 1, w_max);
+    bool updated = false;
+    do {
+        float R[9];
+        quat_rot(T.q, R);
+        const float pwx = V.origin[0] + V.voxel * ((float)x + 0.5f) - T.t[0];
+        const float pwy = V.origin[1] + V.voxel * ((float)y + 0.5f) - T.t[1];
+        const float pwz = V.origin[2] + V.voxel * ((float)z + 0.5f) - T.t[2];
+        // camera frame: R^T (p - t)
+        const float cx = R[0] * pwx + R[3] * pwy + R[6] * pwz;
+        const float cy = R[1] * pwx + R[4] * pwy + R[7] * pwz;
+        const float cz = R[2] * pwx + R[5] * pwy + R[8] * pwz;
+        if (!(cz > 0.f))
+            break;
+        const float u = floorf(K.fx * cx / cz + K.cx + 0.5f);
+        const float v = floorf(K.fy * cy / cz + K.cy + 0.5f);
+        if (!(u >= 0.f && u < (float)K.width && v >= 0.f && v < (float)K.height))
+            break;
+        const float D = __ldg(&depth[(size_t)v * K.width + (size_t)u]);
+        if (!depth_valid(D, K))
+            break;
+        const float sdf = D - cz;
+        if (sdf < -V.trunc)
+            break;
+        const float f = fminf(1.f, sdf / V.trunc);
+        const size_t idx = (size_t)b * BRICK_VOX + l;
+        S *vals = reinterpret_cast<S *>(V.values);
+        const S old = vals[idx];
+        int w_old = V.weights[idx];
+        float F_old = 0.f;
+        if (Enc<DT>::unobserved(old))
+            w_old = 0;
+        else
+            F_old = Enc<DT>::dec(old);
+        const float F_new = ((float)w_old * F_old + f) / (float)(w_old + 1);
+        vals[idx] = Enc<DT>::enc(F_new);
+        V.weights[idx] = (uint8_t)min(w_old + 1, w_max);
+        updated = true;
+    } while (false);
+    // mark the brick so that its packed cells (and those of the cells reaching
+    // into it from the lower neighbours) are rebuilt
+    if (__syncthreads_or(updated) && l == 0)
+        V.dirty[b] = 1;
+}
+
+// Packed trilinear cells of the bricks whose values may have changed: cell i
+// reads voxels i + {0,1}^3, so brick B needs repacking when any of the bricks
+// B + {0,1}^3 is dirty.  One CTA per brick, one thread per cell.  Cells on the
+// upper faces of the volume are never sampled; they copy the nearest voxels.
+template <int DT>
+__global__ void __launch_bounds__(512) pack_cells_kernel(VolumeDesc V, int all)
+{
+    using S = typename Storage<DT>::T;
+    const int b = blockIdx.x;
+    const int bx = b % V.nb[0], by = (b / V.nb[0]) % V.nb[1], bz = b / (V.nb[0] * V.nb[1]);
+    if (!all) {
+        bool need = false;
+        for (int c = 0; c < 8; ++c) {
+            const int nx = bx + (c & 1), ny = by + ((c >> 1) & 1), nz = bz + (c >> 2);
+            if (nx < V.nb[0] && ny < V.nb[1] && nz < V.nb[2])
+                need |= V.dirty[nx + V.nb[0] * (ny + V.nb[1] * nz)] != 0;
+        }
+        if (!need)
+            return;
+    }
+    const int l = threadIdx.x;
+    const int x = bx * BRICK + (l & 7), y = by * BRICK + ((l >> 3) & 7), z = bz * BRICK + (l >> 6);
+    const S *vals = reinterpret_cast<const S *>(V.values);
+    S c[8];
+    for (int k = 0; k < 8; ++k) {
+        const int xx = min(x + (k & 1), V.dim[0] - 1), yy = min(y + ((k >> 1) & 1), V.dim[1] - 1),
+                  zz = min(z + (k >> 2), V.dim[2] - 1);
+        c[k] = vals[brick_index(V, xx, yy, zz)];
+    }
+    const size_t rec = (size_t)b * BRICK_VOX + l;
+    bool all_free = true, any_unobserved = false;
+    if (DT == RF_F32) {
+        float4 *out = reinterpret_cast<float4 *>(V.cells) + 2 * rec;
+        const float *f = reinterpret_cast<const float *>(c);
+        out[0] = make_float4(f[0], f[1], f[2], f[3]);
+        out[1] = make_float4(f[4], f[5], f[6], f[7]);
+        for (int k = 0; k < 8; ++k) {
+            all_free &= f[k] == 1.0f;
+            any_unobserved |= isnan(f[k]);
+        }
+    } else {
+        const uint16_t *h = reinterpret_cast<const uint16_t *>(c);
+        // int16 cells are stored biased (c + 32768) so that decoding needs no sign fix
+        const uint16_t bias = DT == RF_I16 ? 0x8000u : 0u;
+        const uint16_t one = DT == RF_I16 ? 32767u : 0x3C00u;
+        for (int k = 0; k < 8; ++k) {
+            all_free &= h[k] == one;
+            any_unobserved |= DT == RF_I16 ? h[k] == 0x8000u : ((h[k] & 0x7C00u) == 0x7C00u && (h[k] & 0x03FFu));
+        }
+        uint4 r;
+        r.x = (uint32_t)(uint16_t)(h[0] ^ bias) | ((uint32_t)(uint16_t)(h[1] ^ bias) << 16);
+        r.y = (uint32_t)(uint16_t)(h[2] ^ bias) | ((uint32_t)(uint16_t)(h[3] ^ bias) << 16);
+        r.z = (uint32_t)(uint16_t)(h[4] ^ bias) | ((uint32_t)(uint16_t)(h[5] ^ bias) << 16);
+        r.w = (uint32_t)(uint16_t)(h[6] ^ bias) | ((uint32_t)(uint16_t)(h[7] ^ bias) << 16);
+        if (DT == RF_I16 && any_unobserved)
+            r = make_uint4(0u, 0u, 0u, 0u);  // one zero corner test then flags the whole cell invalid
+        reinterpret_cast<uint4 *>(V.cells)[rec] = r;
+    }
+    // brick class: constant free space, all cells invalid, or mixed
+    const bool every_free = __syncthreads_and(all_free) != 0;
+    const bool every_invalid = __syncthreads_and(any_unobserved) != 0;
+    if (l == 0)
+        V.brick_class[b] = every_free ? CELLS_FREE : (every_invalid ? CELLS_INVALID : CELLS_MIXED);
+}
+
+// Rebuild the packed cells after the values changed (all = every brick, else
+// the dirty ones), then clear the dirty flags.  Stream-ordered, capturable.
+rf_status pack_cells(const VolumeDesc &V, int all, cudaStream_t s)
+{
+    const int nbricks = V.nb[0] * V.nb[1] * V.nb[2];
+    switch (V.dtype) {
+    case RF_F32:
+        pack_cells_kernel<RF_F32><<<nbricks, 512, 0, s>>>(V, all);
+        break;
+    case RF_F16:
+        pack_cells_kernel<RF_F16><<<nbricks, 512, 0, s>>>(V, all);
+        break;
+    default:
+        pack_cells_kernel<RF_I16><<<nbricks, 512, 0, s>>>(V, all);
+        break;
+    }
+    RF_CUDA(cudaGetLastError());
+    RF_CUDA(cudaMemsetAsync(V.dirty, 0, (size_t)nbricks, s));
+    return RF_OK;
 }
 
 static rf_status integrate_any(const VolumeDesc &V, const float *depth, const Intr &K, const Pose &T,
@@ -189,7 +283,7 @@ static rf_status integrate_any(const VolumeDesc &V, const float *depth, const In
         break;
     }
     RF_CUDA(cudaGetLastError());
-    return RF_OK;
+    return pack_cells(V, 0, s);
 }
 
 rf_status launch_integrate(const VolumeDesc &V, const float *depth, const Intr &K, const Pose &T, cudaStream_t s)
@@ -234,6 +328,7 @@ rf_status rf_volume_create(int dx, int dy, int dz, float voxel, float trunc, con
                  "dims must be positive multiples of 8 up to 2048");
     RF_CHECK_ARG(voxel > 0.f && trunc > 0.f, "voxel and trunc must be positive");
     RF_CHECK_ARG(dtype == RF_F32 || dtype == RF_F16 || dtype == RF_I16, "unknown dtype");
+    RF_CHECK_ARG((size_t)dx * dy * dz < ((size_t)1 << 31), "dim_x * dim_y * dim_z must stay below 2^31");
     rf_volume v = new rf_volume_s();
     memset(v, 0, sizeof *v);
     VolumeDesc &d = v->d;
@@ -250,13 +345,26 @@ rf_status rf_volume_create(int dx, int dy, int dz, float voxel, float trunc, con
     for (int a = 0; a < 3; ++a)
         d.goff[a] = -origin[a] / voxel - 0.5f;
     d.dtype = dtype;
+    d.cell_stride[0] = BRICK_VOX;
+    d.cell_stride[1] = BRICK_VOX * d.nb[0];
+    d.cell_stride[2] = BRICK_VOX * d.nb[0] * d.nb[1];
     v->n_vox = (size_t)dx * dy * dz;
     cudaGetDevice(&v->device);
     cudaError_t e = cudaMalloc(&d.values, v->n_vox * dtype_size(dtype));
     if (e == cudaSuccess)
         e = cudaMalloc(&d.weights, v->n_vox);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&d.cells, v->n_vox * 8 * dtype_size(dtype));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&d.dirty, v->n_vox / BRICK_VOX);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&d.brick_class, v->n_vox / BRICK_VOX);
     if (e != cudaSuccess) {
         cudaFree(d.values);
+        cudaFree(d.weights);
+        cudaFree(d.cells);
+        cudaFree(d.dirty);
+        cudaFree(d.brick_class);
         delete v;
         return cuda_fail(e, "cudaMalloc(volume)");
     }
@@ -276,6 +384,9 @@ void rf_volume_destroy(rf_volume v)
         return;
     cudaFree(v->d.values);
     cudaFree(v->d.weights);
+    cudaFree(v->d.cells);
+    cudaFree(v->d.dirty);
+    cudaFree(v->d.brick_class);
     cudaFree(v->scratch);
     delete v;
 }
@@ -288,6 +399,13 @@ rf_status rf_volume_reset(rf_volume v, void *stream)
     reset_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>((uint32_t *)v->d.values, words, pattern, v->d.weights,
                                                          v->n_vox);
     RF_CUDA(cudaGetLastError());
+    // every packed cell becomes 8 sentinel corners (biased 0 for int16), every
+    // brick is classed invalid, nothing is dirty
+    const uint32_t cell_pattern = v->d.dtype == RF_I16 ? 0u : pattern;
+    reset_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>((uint32_t *)v->d.cells, 8 * words, cell_pattern,
+                                                         v->d.dirty, v->n_vox / BRICK_VOX);
+    RF_CUDA(cudaGetLastError());
+    RF_CUDA(cudaMemsetAsync(v->d.brick_class, CELLS_INVALID, v->n_vox / BRICK_VOX, (cudaStream_t)stream));
     return RF_OK;
 }
 
@@ -332,6 +450,8 @@ rf_status rf_volume_upload(rf_volume v, const void *values_host, const uint8_t *
             linear_to_brick<uint16_t><<<blocks, threads>>>(v->d, (const uint16_t *)tmp, wtmp,
                                                            (uint16_t *)v->d.values, v->d.weights);
         e = cudaGetLastError();
+        if (e == cudaSuccess && pack_cells(v->d, 1, nullptr) != RF_OK)
+            e = cudaGetLastError();
         if (e == cudaSuccess)
             e = cudaDeviceSynchronize();
     }

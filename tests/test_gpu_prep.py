@@ -137,6 +137,33 @@ def test_integrate_parity_sequence(oracle, nat, dtype):
         assert np.mean(np.abs(Fg[both] - ov.F[both]) < 0.5 / 32767 + 1e-9) > 0.99
 
 
+def test_dirty_brick_repacking_matches_full_pack(nat):
+    """Fusion repacks only the trilinear cells of bricks it touched; a volume that
+    receives the same values by upload (full repack) must score identically."""
+    import torch
+
+    cfg = dict(synth.CONFIGS["tiny"])
+    dims, voxel, trunc = cfg["dims"], cfg["voxel"], cfg["trunc"]
+    scene = synth.make_scene(dims * voxel, cfg["wall_inset"], 0)
+    traj = synth.make_trajectory(scene, 4, 3.0, 3.0, 0)
+    K = synth.intrinsics(cfg["width"], cfg["height"])
+    for dtype in ("i16", "f16", "f32"):
+        a = nat.Volume(dims, voxel, trunc, (0, 0, 0), dtype)
+        for f in range(4):
+            nat.tsdf_integrate(a, torch.from_numpy(synth.render_depth(scene, traj[f], K)).cuda(), K, traj[f])
+        codes, w = a.download()
+        b = nat.Volume(dims, voxel, trunc, (0, 0, 0), dtype)
+        b.upload(codes, w)
+        d = torch.from_numpy(synth.render_depth(scene, traj[2], K)).cuda()
+        pts = nat.rf_depth_to_points(d, K, 1)
+        pts = pts[pts[:, 3] > 0].contiguous()
+        pst = nat.pst_create(512, seed=4)
+        ra = nat.fitness_eval(a, pts, pst, traj[1], [0.05] * 6, nat.make_params())
+        rb = nat.fitness_eval(b, pts, pst, traj[1], [0.05] * 6, nat.make_params())
+        for x, y in zip(ra, rb):
+            np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
+
+
 def test_integrate_skips_invalid_depth(nat):
     import torch
 

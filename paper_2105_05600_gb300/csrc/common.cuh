@@ -265,49 +265,84 @@ __device__ __forceinline__ void cell_locate(const VolumeDesc &V, float gx, float
     c.cls = inside ? (unsigned)__ldg(&V.brick_class[brick]) : (unsigned)CELLS_INVALID;
 }
 
+// The record of a constant brick is not loaded: the registers get a fill
+// record that evaluates to the same answer (eight +1 corners for free space,
+// an invalid record otherwise), and the load is predicated on a mixed brick.
+__device__ __forceinline__ void ldg_v4_if(bool p, const void *ptr, uint32_t &x, uint32_t &y, uint32_t &z, uint32_t &w)
+{
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t@p ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%5];\n\t}"
+        : "+r"(x), "+r"(y), "+r"(z), "+r"(w)
+        : "r"((int)p), "l"(ptr));
+}
+
 template <int DT> __device__ __forceinline__ void cell_fetch(const VolumeDesc &V, const CellRef &c, CellData<DT> &d)
 {
+    const bool mixed = c.cls == CELLS_MIXED, free_space = c.cls == CELLS_FREE;
     if constexpr (DT == RF_F32) {
+        // +1.0f for free space, NaN (invalid) otherwise
+        const uint32_t f = free_space ? 0x3F800000u : 0x7FC00000u;
+        uint32_t a0 = f, a1 = f, a2 = f, a3 = f, b0 = f, b1 = f, b2 = f, b3 = f;
         const float4 *cp = reinterpret_cast<const float4 *>(V.cells) + 2 * (size_t)c.rec;
-        d.a = c.cls == CELLS_MIXED ? __ldg(cp) : make_float4(0.f, 0.f, 0.f, 0.f);
-        d.b = c.cls == CELLS_MIXED ? __ldg(cp + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        ldg_v4_if(mixed, cp, a0, a1, a2, a3);
+        ldg_v4_if(mixed, cp + 1, b0, b1, b2, b3);
+        d.a = make_float4(__uint_as_float(a0), __uint_as_float(a1), __uint_as_float(a2), __uint_as_float(a3));
+        d.b = make_float4(__uint_as_float(b0), __uint_as_float(b1), __uint_as_float(b2), __uint_as_float(b3));
     } else {
-        d.a = c.cls == CELLS_MIXED ? __ldg(reinterpret_cast<const uint4 *>(V.cells) + c.rec) : make_uint4(1u, 0u, 0u, 0u);
+        // int16 (biased): 0xFFFF = code +32767, 0 = invalid; half: 1.0h pairs, NaN pairs
+        const uint32_t f = DT == RF_I16 ? (free_space ? 0xFFFFFFFFu : 0u) : (free_space ? 0x3C003C00u : 0x7E007E00u);
+        uint32_t x = f, y = f, z = f, w = f;
+        ldg_v4_if(mixed, reinterpret_cast<const uint4 *>(V.cells) + c.rec, x, y, z, w);
+        d.a = make_uint4(x, y, z, w);
     }
 }
 
 template <int DT> __device__ __forceinline__ bool cell_eval(const CellRef &c, const CellData<DT> &d, float &psi)
 {
-    float k[8];
-    bool ok_mixed;
-    if constexpr (DT == RF_F32) {
-        k[0] = d.a.x; k[1] = d.a.y; k[2] = d.a.z; k[3] = d.a.w;
-        k[4] = d.b.x; k[5] = d.b.y; k[6] = d.b.z; k[7] = d.b.w;
-    } else if constexpr (DT == RF_I16) {
-        decode_i16x2(d.a.x, k[0], k[1]);
-        decode_i16x2(d.a.y, k[2], k[3]);
-        decode_i16x2(d.a.z, k[4], k[5]);
-        decode_i16x2(d.a.w, k[6], k[7]);
-    } else {
-        const uint32_t w[4] = {d.a.x, d.a.y, d.a.z, d.a.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&w[q]));
-            k[2 * q] = f2.x;
-            k[2 * q + 1] = f2.y;
-        }
-    }
-    const float c00 = lerp1(k[0], k[1], c.fx), c10 = lerp1(k[2], k[3], c.fx);
-    const float c01 = lerp1(k[4], k[5], c.fx), c11 = lerp1(k[6], k[7], c.fx);
-    float v = lerp1(lerp1(c00, c10, c.fy), lerp1(c01, c11, c.fy), c.fz);
+    float c00, c10, c01, c11;
+    bool ok;
     if constexpr (DT == RF_I16) {
-        v *= 1.0f / I16_SCALE;
-        ok_mixed = (d.a.x & 0xFFFFu) != 0u;  // all-zero record = some corner unobserved
+        // biased floats 2^23 + u: differences are exact, so the first lerp level
+        // takes its base unbiased and its slope from the biased pair
+        const float B = 8421376.0f;  // 2^23 + 32768
+        const float a0 = __int_as_float((int)__byte_perm(d.a.x, 0x4B00u, 0x5410));
+        const float a1 = __int_as_float((int)__byte_perm(d.a.x, 0x4B00u, 0x5432));
+        const float a2 = __int_as_float((int)__byte_perm(d.a.y, 0x4B00u, 0x5410));
+        const float a3 = __int_as_float((int)__byte_perm(d.a.y, 0x4B00u, 0x5432));
+        const float a4 = __int_as_float((int)__byte_perm(d.a.z, 0x4B00u, 0x5410));
+        const float a5 = __int_as_float((int)__byte_perm(d.a.z, 0x4B00u, 0x5432));
+        const float a6 = __int_as_float((int)__byte_perm(d.a.w, 0x4B00u, 0x5410));
+        const float a7 = __int_as_float((int)__byte_perm(d.a.w, 0x4B00u, 0x5432));
+        c00 = fmaf(c.fx, a1 - a0, a0 - B);
+        c10 = fmaf(c.fx, a3 - a2, a2 - B);
+        c01 = fmaf(c.fx, a5 - a4, a4 - B);
+        c11 = fmaf(c.fx, a7 - a6, a6 - B);
+        ok = (d.a.x & 0xFFFFu) != 0u;  // all-zero record = some corner unobserved
     } else {
-        ok_mixed = !isnan(v);
+        float k[8];
+        if constexpr (DT == RF_F32) {
+            k[0] = d.a.x; k[1] = d.a.y; k[2] = d.a.z; k[3] = d.a.w;
+            k[4] = d.b.x; k[5] = d.b.y; k[6] = d.b.z; k[7] = d.b.w;
+        } else {
+            const uint32_t w[4] = {d.a.x, d.a.y, d.a.z, d.a.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&w[q]));
+                k[2 * q] = f2.x;
+                k[2 * q + 1] = f2.y;
+            }
+        }
+        c00 = lerp1(k[0], k[1], c.fx);
+        c10 = lerp1(k[2], k[3], c.fx);
+        c01 = lerp1(k[4], k[5], c.fx);
+        c11 = lerp1(k[6], k[7], c.fx);
     }
-    psi = c.cls == CELLS_MIXED ? v : free_psi<DT>();
-    return c.cls == CELLS_MIXED ? ok_mixed : c.cls == CELLS_FREE;
+    float v = lerp1(lerp1(c00, c10, c.fy), lerp1(c01, c11, c.fy), c.fz);
+    if constexpr (DT == RF_I16)
+        v *= 1.0f / I16_SCALE;
+    else
+        ok = !isnan(v);  // a NaN corner poisons the interpolation
+    psi = v;
+    return ok;
 }
 
 }  // namespace rf

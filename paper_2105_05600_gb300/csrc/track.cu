@@ -30,7 +30,10 @@ Pose to_pose(const rf_pose &p);
 constexpr int FIT_THREADS = 256;
 constexpr int FIT_WARPS = FIT_THREADS / 32;
 constexpr int CHUNK_MAX = 256;        // points staged per warp (16 B each)
-constexpr int UNITS_PER_WARP = 16;    // target work units per warp and iteration
+#ifndef RF_UNITS_PER_WARP
+#define RF_UNITS_PER_WARP 16
+#endif
+constexpr int UNITS_PER_WARP = RF_UNITS_PER_WARP;  // target work units per warp and iteration
 constexpr int APW = 16;               // doubles per CTA in the APS partials
 constexpr int MAX_CTAS_PER_SM = 2048 / FIT_THREADS;  // bound for grid-sized scratch
 // CTAs of the persistent kernel resident per SM (register budget 65536 / (256 * n))
@@ -95,6 +98,10 @@ struct FitParams {
     int l1, right_mult;
 };
 
+template <int DT, int MODE, bool L1>
+__device__ __forceinline__ void fitness_points(const VolumeDesc &V, const float4 *spts, int cnt, const float R[9],
+                                               float t0, float t1, float t2, float &sum, float &comp, int &nv);
+
 // Lane `lane` of a warp scores particle i over the points staged in `spts`
 // [0, cnt): S = sum psi^2 (|psi| with L1), psi = 1 for invalid samples.
 template <int DT, int MODE>
@@ -120,8 +127,21 @@ __device__ __forceinline__ void fitness_lane(const VolumeDesc &V, const float4 *
     const float t0 = fmaf(P.t[0], s, V.goff[0]), t1 = fmaf(P.t[1], s, V.goff[1]), t2 = fmaf(P.t[2], s, V.goff[2]);
     float sum = 0.f, comp = 0.f;
     int nv = 0;
+    if (fp.l1)
+        fitness_points<DT, MODE, true>(V, spts, cnt, R, t0, t1, t2, sum, comp, nv);
+    else
+        fitness_points<DT, MODE, false>(V, spts, cnt, R, t0, t1, t2, sum, comp, nv);
+    S_out = (double)sum + (double)comp;
+    n_out = nv;
+}
+
+// The point loop of one lane: lookups of points [0, cnt) under the grid-space
+// pose (R, t), accumulated as psi^2 (|psi| with L1), psi = 1 when invalid.
+template <int DT, int MODE, bool L1>
+__device__ __forceinline__ void fitness_points(const VolumeDesc &V, const float4 *spts, int cnt, const float R[9],
+                                               float t0, float t1, float t2, float &sum, float &comp, int &nv)
+{
     int j = 0;
-    const bool l1 = fp.l1 != 0;
     auto add = [&](float grp) {
         if (Mode<MODE>::plain)
             sum += grp;
@@ -131,7 +151,7 @@ __device__ __forceinline__ void fitness_lane(const VolumeDesc &V, const float4 *
     auto term = [&](bool ok, float psi) {
         nv += ok ? 1 : 0;
         psi = ok ? psi : 1.f;
-        return l1 ? fabsf(psi) : psi * psi;
+        return L1 ? fabsf(psi) : psi * psi;
     };
     if (!Mode<MODE>::nearest) {
         // groups of 4 lookups: all class loads, then all cell loads, then the
@@ -178,8 +198,6 @@ __device__ __forceinline__ void fitness_lane(const VolumeDesc &V, const float4 *
         }
         add(term(ok, psi));
     }
-    S_out = (double)sum + (double)comp;
-    n_out = nv;
 }
 
 // Work decomposition shared by the standalone and the persistent kernels: unit

@@ -90,6 +90,9 @@ def _load():
             lib.or_grid_search.argtypes = [D, I, d, D, D, I, i, D, D, i, d, i, D]
             lib.or_grid_search.restype = d
             lib.or_fitness_fragile.argtypes = [D, I, d, D, D, I, i, D, d, i, d, D, I, I, D, I]
+            lib.or_pfo_frame_sched.argtypes = [D, I, d, D, i, I, ctypes.POINTER(D), I, F, i, i, d, d, d, d, d, d, D,
+                                               D, D, F, i, d, d, d, d, i, i, D, D, D, I]
+            lib.or_pfo_frame_sched.restype = i
             lib.or_tsdf_integrate_ambiguity.argtypes = [I, d, D, d, F, i, i, d, d, d, d, d, d, D, d, I]
             _lib = lib
     return _lib
@@ -279,6 +282,37 @@ class Volume:
         rho = lib.or_grid_search(self.F.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pdim, self.voxel, por, pp,
                                  pin, pts.shape[0], pc, ph, int(steps), float(tau), int(flags), pb)
         return rho, best
+
+    def pfo_frame_sched(self, level_pts, level_n, prev_depth, K, pose_prev, c0, r0, omega, params):
+        """Algorithm 1 with multi-resolution alternation (Sec. 4): level l uses the
+        first level_n[l] template rows and the point set level_pts[l].  Same
+        return value as pfo_frame; trace rows add the level (col 30) and N_l (31)."""
+        lib = _load()
+        L = len(level_pts)
+        arrs = [np.ascontiguousarray(p, dtype=np.float64) for p in level_pts]
+        ptrs = (ctypes.POINTER(ctypes.c_double) * L)(*[a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs])
+        ln, pln = _i(np.asarray(level_n, np.int32))
+        lm, plm = _i(np.array([a.shape[0] for a in arrs], np.int32))
+        prev_depth, pdp = _f(prev_depth)
+        H, W = prev_depth.shape
+        pose_prev, ppv = _d(pose_prev)
+        c0, pc0 = _d(c0)
+        r0, pr0 = _d(r0)
+        omega, pom = _f(omega)
+        N = omega.shape[1]
+        k_max = int(params["k_max"])
+        _, pdim = _i(self.dims)
+        _, por = _d(self.origin)
+        pose, ppo = _d(np.zeros(7))
+        r1, pr1 = _d(np.zeros(6))
+        trace, ptr = _d(np.zeros((k_max, TRACE_STRIDE)))
+        iters = ctypes.c_int(0)
+        st = lib.or_pfo_frame_sched(self.F.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pdim, self.voxel, por, L,
+                                    pln, ptrs, plm, pdp, W, H, K["fx"], K["fy"], K["cx"], K["cy"], K["z_min"],
+                                    K["z_max"], ppv, pc0, pr0, pom, N, float(params["tau"]), float(params["beta"]),
+                                    float(params["eps"]), float(params["stop_eps"]), k_max, int(params["flags"]), ppo,
+                                    pr1, ptr, ctypes.byref(iters))
+        return dict(status=st, pose=pose, r1=r1, iters=iters.value, trace=trace[:iters.value])
 
     def pfo_frame(self, pts, prev_depth, K, pose_prev, c0, r0, omega, params):
         """Algorithm 1 for one frame.  params: dict(tau, beta, eps, stop_eps, k_max, flags).

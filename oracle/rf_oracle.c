@@ -916,3 +916,159 @@ void or_tsdf_integrate_ambiguity(const int dim[3], double voxel, const double or
                 ambig[idx] = a;
             }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Multi-resolution PST alternation (Sec. 4 "Multi-resolution PST").          */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Algorithm 1 with L (particle count, depth stride) levels used in turn:
+ * iteration k uses level l = (k - 1) mod L, i.e. the first level_n[l] rows of
+ * the template and the points unprojected at that level's stride
+ * (level_pts[l], level_M[l] points).  Readings: with L > 1 the fitness of
+ * consecutive iterations is normalised over different point sets, so the APS
+ * threshold is the fitness of the centre particle in the current iteration
+ * (particle 0); with L = 1 the rule of or_pfo_frame applies.  Everything else
+ * (overlap with s*_{k-1}, Eq. ebs / wafit / rsdir / rsinter / momentum, the
+ * corner cases and stop rules) is that of or_pfo_frame.  Same outputs.
+ */
+int or_pfo_frame_sched(const double *F, const int dim[3], double voxel, const double origin[3], int L,
+                       const int *level_n, const double *const *level_pts, const int *level_M,
+                       const float *prev_depth, int W, int H, double fx, double fy, double cx, double cy,
+                       double z_min, double z_max, const double pose_prev[7], const double c0[7], const double r0[6],
+                       const float *omega, int N, double tau, double beta, double eps, double stop_eps, int k_max,
+                       int flags, double pose_out[7], double r1_out[6], double *trace, int *iters_out)
+{
+    if (L < 1 || N < 1 || k_max < 1)
+        return OR_ERR_ARG;
+    int M_max = 1, N_lev_max = 1;
+    for (int l = 0; l < L; ++l) {
+        if (level_n[l] < 1 || level_n[l] > N)
+            return OR_ERR_ARG;
+        if (level_M[l] > M_max)
+            M_max = level_M[l];
+        if (level_n[l] > N_lev_max)
+            N_lev_max = level_n[l];
+    }
+    for (int d = 0; d < 6; ++d)
+        if (omega[(size_t)d * N] != 0.0f)
+            return OR_ERR_ARG;
+    int *mask = (int *)malloc(sizeof(int) * (size_t)M_max);
+    double *margin = (double *)malloc(sizeof(double) * (size_t)M_max);
+    double *rho = (double *)malloc(sizeof(double) * (size_t)N_lev_max);
+    double *delta = (double *)malloc(sizeof(double) * 6 * (size_t)N_lev_max);
+    double c[7], r[6], rho_carry = 0.0;
+    memcpy(c, c0, sizeof c);
+    memcpy(r, r0, sizeof r);
+    int empty_run = 0, status = OR_OK, k = 0;
+    for (k = 1; k <= k_max; ++k) {
+        const int l = (k - 1) % L;
+        const int Nl = level_n[l], M = level_M[l];
+        const double *pts = level_pts[l];
+        int nO = 0;
+        double min_margin = INFINITY;
+        if (flags & OR_OVERLAP) {
+            nO = or_overlap(pts, M, prev_depth, W, H, fx, fy, cx, cy, z_min, z_max, c, pose_prev, mask, margin);
+            for (int j = 0; j < M; ++j)
+                if (pts[4 * (size_t)j + 3] != 0.0 && margin[j] < min_margin)
+                    min_margin = margin[j];
+        } else {
+            for (int j = 0; j < M; ++j) {
+                mask[j] = pts[4 * (size_t)j + 3] != 0.0;
+                nO += mask[j];
+            }
+        }
+        double *tr = trace ? trace + OR_TRACE_STRIDE * (size_t)(k - 1) : NULL;
+        if (nO == 0) {
+            status = OR_ERR_EMPTY;
+            if (tr) {
+                memset(tr, 0, sizeof(double) * OR_TRACE_STRIDE);
+                tr[0] = k;
+                tr[28] = 4;
+            }
+            break;
+        }
+        double rho_max = -1.0, rho_2nd = -1.0;
+        int argmax = 0;
+        for (int i = 0; i < Nl; ++i) {
+            double pose[7], S;
+            int n, nOi;
+            for (int d = 0; d < 6; ++d)
+                delta[6 * (size_t)i + d] = r[d] * omega[(size_t)d * N + i];
+            or_compose_offset(c, delta + 6 * (size_t)i, flags, pose);
+            or_fitness(F, dim, voxel, origin, pts, mask, M, pose, tau, flags, &S, &n, &nOi, &rho[i]);
+            if (rho[i] > rho_max) {
+                rho_2nd = rho_max;
+                rho_max = rho[i];
+                argmax = i;
+            } else if (rho[i] > rho_2nd) {
+                rho_2nd = rho[i];
+            }
+        }
+        const int centre_ref = (k == 1) || (flags & OR_RHO_REF_CENTER) || (L > 1);
+        double rho_ref = centre_ref ? rho[0] : rho_carry;
+        double min_gap = INFINITY;
+        for (int i = 1; i < Nl; ++i)
+            if (fabs(rho[i] - rho_ref) < min_gap)
+                min_gap = fabs(rho[i] - rho_ref);
+        double dbar[6], rho_tilde, r_new[6];
+        int n_aps = or_pst_update(Nl, rho, delta, rho_ref, r, beta, eps, dbar, &rho_tilde, r_new);
+        double s_new[7];
+        if (n_aps > 0) {
+            or_compose_offset(c, dbar, flags, s_new);
+            empty_run = 0;
+        } else {
+            memcpy(s_new, c, sizeof s_new);
+            ++empty_run;
+        }
+        rho_carry = rho_tilde;
+        memcpy(c, s_new, sizeof c);
+        memcpy(r, r_new, sizeof r);
+        if (k == 1)
+            memcpy(r1_out, r, sizeof r);
+        double step = 0.0;
+        for (int d = 0; d < 6; ++d)
+            step = fmax(step, fabs(dbar[d]));
+        int stop = 0;
+        if (empty_run >= 2)
+            stop = 1;
+        else if (n_aps > 0 && step < stop_eps)
+            stop = 2;
+        else if (k == k_max)
+            stop = 3;
+        if (tr) {
+            tr[0] = k;
+            tr[1] = nO;
+            tr[2] = n_aps;
+            tr[3] = rho_ref;
+            tr[4] = rho_tilde;
+            tr[5] = rho_max;
+            tr[6] = argmax;
+            for (int a = 0; a < 7; ++a)
+                tr[7 + a] = c[a];
+            for (int d = 0; d < 6; ++d) {
+                tr[14 + d] = r[d];
+                tr[20 + d] = dbar[d];
+            }
+            tr[26] = min_gap;
+            tr[27] = min_margin;
+            tr[28] = stop;
+            tr[29] = rho_2nd;
+            tr[30] = l;
+            tr[31] = Nl;
+        }
+        if (stop)
+            break;
+    }
+    if (k > k_max)
+        k = k_max;
+    memcpy(pose_out, c, sizeof c);
+    if (k == 1 && status == OR_ERR_EMPTY)
+        memcpy(r1_out, r0, sizeof r);
+    *iters_out = k;
+    free(mask);
+    free(margin);
+    free(rho);
+    free(delta);
+    return status;
+}

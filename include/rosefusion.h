@@ -89,6 +89,8 @@ typedef struct {
     float scale[6]; /* r_k                                   */
     float offset[6];/* delta_bar_k = s*_k - s*_{k-1} (local) */
     int stop;       /* 0 running, 1 empty twice, 2 small step, 3 k_max, 4 empty overlap */
+    int level;      /* multi-resolution level used by this iteration          */
+    int n_particles;/* particles scored (the level's prefix of the template)  */
 } rf_iter_stats;
 
 typedef struct {
@@ -264,6 +266,19 @@ rf_status rf_tracker_get_scale(rf_tracker tr, float r_host[6]);
 rf_status rf_tracker_set_scale(rf_tracker tr, const float r_host[6]);
 /* Replace the parameter block (k_max <= RF_MAX_ITERS). */
 rf_status rf_tracker_set_params(rf_tracker tr, const rf_params *p);
+/*
+ * rf_tracker_set_schedule -- multi-resolution PST alternation (Sec. 4,
+ * "Multi-resolution PST"): iteration k uses level (k - 1) mod n_levels, i.e.
+ * the first n[level] particles of the template and the depth points at
+ * stride[level].  1 <= n_levels <= RF_MAX_LEVELS, 1 <= n[l] <= template size,
+ * stride[l] >= 1.  With more than one level the APS threshold of every
+ * iteration is the fitness of the centre particle (consecutive iterations
+ * normalise over different point sets).  The default schedule is one level:
+ * the whole template at rf_params.stride.  Reallocates the tracker's point
+ * and partial-sum buffers (synchronous).
+ */
+#define RF_MAX_LEVELS 4
+rf_status rf_tracker_set_schedule(rf_tracker tr, int n_levels, const int *n, const int *stride);
 
 /*
  * pfo_track_frame_async -- Algorithm 1 for one frame in ONE persistent kernel
@@ -316,6 +331,50 @@ rf_status rf_sequence_start(rf_tracker tr, const float *depth, int depth_on_host
                             const rf_pose *pose, void *stream);
 rf_status rf_sequence_step(rf_tracker tr, const float *depth, int depth_on_host, const rf_intrinsics *K,
                            rf_pose *out_pose_host, float *out_pose_dev, rf_frame_stats *stats_dev, void *stream);
+
+/* ------------------------------------------------------------------ batch --- */
+/*
+ * A batch steps up to RF_MAX_BATCH independent sequences (trackers in sequence
+ * mode, each with its own volume, template, schedule and frame size) by one
+ * frame per rf_batch_step: ONE persistent kernel runs the PFO iterations of
+ * every sequence (work units of all sequences share the grid; a sequence that
+ * has stopped takes no further work), then each frame is fused.  All trackers
+ * must use the same volume dtype and the same RF_NEAREST / RF_COMPENSATED
+ * flags.  The trackers' depth and pose rings (two slots) hold the frames:
+ * frame f of sequence i lives in slot f % 2.
+ *   rf_batch_depth_slot  device address where the caller writes frame f of
+ *                        sequence i (float[H_i * W_i]) before the step for f
+ *   rf_batch_start       fuse the slot-0 frames at the given host poses
+ *   rf_batch_step        track the frames of slot `parity` against slot
+ *                        1 - parity and fuse them; use_graph != 0 replays a
+ *                        CUDA graph captured on first use for this parity and
+ *                        launch configuration (capture happens on an internal
+ *                        stream; the graph is launched on `stream`)
+ *   rf_batch_pose_dev    device float[7]: the pose of sequence i in slot parity
+ *   rf_batch_autotune    times the PFO kernel of the frames currently in slot
+ *                        `parity` for each candidate launch shape (CTAs per SM)
+ *                        and work granularity, keeps the fastest and returns
+ *                        its time (ms); inputs and tracker state are restored,
+ *                        the volumes are not touched
+ * Asynchronous except rf_batch_create / rf_batch_autotune.
+ */
+#define RF_MAX_BATCH 16
+typedef struct rf_batch_s *rf_batch;
+typedef struct {
+    int ctas_per_sm;  /* resident CTAs of 256 threads per SM                            */
+    int work_warps;   /* warp count the work split targets (units of ~16 per warp)      */
+    float ms;         /* measured PFO kernel time of the chosen configuration (autotune) */
+} rf_launch_config;
+rf_status rf_batch_create(const rf_tracker *trackers, int n, const rf_intrinsics *K, rf_batch *out);
+void rf_batch_destroy(rf_batch b);
+rf_status rf_batch_depth_slot(rf_batch b, int i, int parity, float **depth_dev);
+rf_status rf_batch_pose_dev(rf_batch b, int i, int parity, float **pose_dev);
+rf_status rf_batch_start(rf_batch b, const rf_pose *poses_host, void *stream);
+rf_status rf_batch_step(rf_batch b, int parity, int use_graph, void *stream);
+rf_status rf_batch_autotune(rf_batch b, int parity, rf_launch_config *chosen, void *stream);
+rf_status rf_batch_set_config(rf_batch b, const rf_launch_config *cfg);
+/* Per-sequence frame statistics of the last step (device rf_frame_stats[n]). */
+rf_status rf_batch_stats_dev(rf_batch b, rf_frame_stats **stats_dev);
 
 /* Test hook: make block 0 of the next persistent launch leave without arriving
  * at its first grid barrier, with barrier waits limited to timeout_ms; the

@@ -49,7 +49,12 @@ class rf_iter_stats(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("n_overlap", ctypes.c_int), ("n_aps", ctypes.c_int), ("argmax", ctypes.c_int),
                 ("rho_ref", ctypes.c_float), ("rho_tilde", ctypes.c_float), ("rho_max", ctypes.c_float),
                 ("rho_second", ctypes.c_float), ("pose", ctypes.c_float * 7), ("scale", ctypes.c_float * 6),
-                ("offset", ctypes.c_float * 6), ("stop", ctypes.c_int)]
+                ("offset", ctypes.c_float * 6), ("stop", ctypes.c_int), ("level", ctypes.c_int),
+                ("n_particles", ctypes.c_int)]
+
+
+class rf_launch_config(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("work_warps", ctypes.c_int), ("ms", ctypes.c_float)]
 
 
 class rf_frame_stats(ctypes.Structure):
@@ -62,8 +67,11 @@ EXPORTS = ["rf_last_error", "rf_version", "pst_create", "rf_volume_create", "rf_
            "rf_volume_upload", "rf_volume_download", "rf_volume_info", "tsdf_integrate", "tsdf_integrate_dev",
            "rf_depth_to_points",
            "rf_overlap_mask", "fitness_eval", "fitness_eval_noalloc", "rf_tracker_create", "rf_tracker_destroy", "rf_tracker_get_scale",
-           "rf_tracker_set_scale", "rf_tracker_set_params", "pfo_track_frame_async", "pfo_track_frame",
-           "rf_tracker_last_status", "rf_sequence_start", "rf_sequence_step", "rf_tracker_debug_skip_barrier"]
+           "rf_tracker_set_scale", "rf_tracker_set_params", "rf_tracker_set_schedule", "pfo_track_frame_async",
+           "pfo_track_frame", "rf_tracker_last_status", "rf_sequence_start", "rf_sequence_step",
+           "rf_tracker_debug_skip_barrier", "rf_batch_create", "rf_batch_destroy", "rf_batch_depth_slot",
+           "rf_batch_pose_dev", "rf_batch_start", "rf_batch_step", "rf_batch_autotune", "rf_batch_set_config",
+           "rf_batch_stats_dev"]
 
 
 def _load():
@@ -103,6 +111,16 @@ def _load():
         "rf_sequence_start": (i, [P, P, i, ctypes.POINTER(rf_intrinsics), ctypes.POINTER(rf_pose), P]),
         "rf_sequence_step": (i, [P, P, i, ctypes.POINTER(rf_intrinsics), ctypes.POINTER(rf_pose), P, P, P]),
         "rf_tracker_debug_skip_barrier": (i, [P, i, i]),
+        "rf_tracker_set_schedule": (i, [P, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "rf_batch_create": (i, [ctypes.POINTER(P), i, ctypes.POINTER(rf_intrinsics), ctypes.POINTER(P)]),
+        "rf_batch_destroy": (None, [P]),
+        "rf_batch_depth_slot": (i, [P, i, i, ctypes.POINTER(P)]),
+        "rf_batch_pose_dev": (i, [P, i, i, ctypes.POINTER(P)]),
+        "rf_batch_start": (i, [P, ctypes.POINTER(rf_pose), P]),
+        "rf_batch_step": (i, [P, i, i, P]),
+        "rf_batch_autotune": (i, [P, i, ctypes.POINTER(rf_launch_config), P]),
+        "rf_batch_set_config": (i, [P, ctypes.POINTER(rf_launch_config)]),
+        "rf_batch_stats_dev": (i, [P, ctypes.POINTER(P)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -165,7 +183,8 @@ def stats_dict(s: rf_frame_stats) -> dict:
         r = s.it[k]
         rows.append(dict(k=r.k, n_overlap=r.n_overlap, n_aps=r.n_aps, argmax=r.argmax, rho_ref=r.rho_ref,
                          rho_tilde=r.rho_tilde, rho_max=r.rho_max, rho_second=r.rho_second, pose=list(r.pose),
-                         scale=list(r.scale), offset=list(r.offset), stop=r.stop))
+                         scale=list(r.scale), offset=list(r.offset), stop=r.stop, level=r.level,
+                         n_particles=r.n_particles))
     return dict(iters=s.iters, status=s.status, n_points=s.n_points, lookups=s.lookups, r1=list(s.r1), it=rows)
 
 
@@ -362,6 +381,91 @@ class Tracker:
 
     def debug_skip_barrier(self, enable: bool, timeout_ms: int):
         _check(lib.rf_tracker_debug_skip_barrier(self.handle, int(bool(enable)), int(timeout_ms)))
+
+    def set_schedule(self, n, stride):
+        """Multi-resolution alternation: level l scores the first n[l] particles on
+        the points at stride[l] (Sec. 4)."""
+        L = len(n)
+        _check(lib.rf_tracker_set_schedule(self.handle, L, (ctypes.c_int * L)(*[int(x) for x in n]),
+                                           (ctypes.c_int * L)(*[int(x) for x in stride])))
+
+
+class Batch:
+    """Owning wrapper of an rf_batch: up to RF_MAX_BATCH sequences stepped together."""
+
+    def __init__(self, trackers, Ks):
+        n = len(trackers)
+        hs = (ctypes.c_void_p * n)(*[t.handle.value for t in trackers])
+        Karr = (rf_intrinsics * n)(*[make_intrinsics(K) for K in Ks])
+        h = ctypes.c_void_p()
+        _check(lib.rf_batch_create(hs, n, Karr, ctypes.byref(h)))
+        self.handle = h
+        self.trackers = list(trackers)
+        self.Ks = [dict(K) for K in Ks]
+        self.n = n
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.rf_batch_destroy(h)
+            self.handle = None
+
+    def depth_slot(self, i, parity):
+        """A torch view of the device slot that must hold frame f (f % 2 == parity) of sequence i."""
+        import torch
+
+        ptr = ctypes.c_void_p()
+        _check(lib.rf_batch_depth_slot(self.handle, int(i), int(parity), ctypes.byref(ptr)))
+        return _view_device(ptr.value, (self.Ks[i]["height"], self.Ks[i]["width"]), torch.float32)
+
+    def pose_dev(self, i, parity):
+        import torch
+
+        ptr = ctypes.c_void_p()
+        _check(lib.rf_batch_pose_dev(self.handle, int(i), int(parity), ctypes.byref(ptr)))
+        return _view_device(ptr.value, (7,), torch.float32)
+
+    def stats(self):
+        """Host rf_frame_stats dicts of the last step, one per sequence."""
+        import torch
+
+        ptr = ctypes.c_void_p()
+        _check(lib.rf_batch_stats_dev(self.handle, ctypes.byref(ptr)))
+        raw = _view_device(ptr.value, (self.n * ctypes.sizeof(rf_frame_stats),), torch.uint8).cpu().numpy().tobytes()
+        sz = ctypes.sizeof(rf_frame_stats)
+        return [stats_dict(rf_frame_stats.from_buffer_copy(raw[i * sz:(i + 1) * sz])) for i in range(self.n)]
+
+    def start(self, poses, stream=None):
+        arr = (rf_pose * self.n)(*[make_pose(p) for p in poses])
+        _check(lib.rf_batch_start(self.handle, arr, _stream(stream)))
+
+    def step(self, parity, use_graph=False, stream=None):
+        _check(lib.rf_batch_step(self.handle, int(parity), int(bool(use_graph)), _stream(stream)))
+
+    def autotune(self, parity, stream=None):
+        cfg = rf_launch_config()
+        _check(lib.rf_batch_autotune(self.handle, int(parity), ctypes.byref(cfg), _stream(stream)))
+        return dict(ctas_per_sm=cfg.ctas_per_sm, work_warps=cfg.work_warps, ms=cfg.ms)
+
+    def set_config(self, ctas_per_sm=0, work_warps=3648):
+        cfg = rf_launch_config(int(ctas_per_sm), int(work_warps), 0.0)
+        _check(lib.rf_batch_set_config(self.handle, ctypes.byref(cfg)))
+
+
+def _view_device(ptr, shape, dtype):
+    """A torch tensor aliasing library-owned device memory (valid while the owner lives)."""
+    import torch
+
+    n = 1
+    for s in shape:
+        n *= s
+    itemsize = torch.tensor([], dtype=dtype).element_size()
+
+    class _CudaArray:
+        __cuda_array_interface__ = {"shape": (n,), "typestr": {1: "|u1", 4: "<f4"}[itemsize],
+                                    "data": (ptr, False), "version": 3}
+
+    return torch.as_tensor(_CudaArray(), device="cuda").view(dtype).reshape(shape)
 
 
 def pfo_track_frame(tr: Tracker, depth, prev_depth, K: dict, prev_pose, stream=None, check=True):

@@ -218,17 +218,36 @@ template <int DT> __device__ __forceinline__ float free_psi()
 
 __device__ __forceinline__ float lerp1(float a, float b, float t) { return fmaf(t, b - a, a); }
 
+// The fields of a volume that the fitness loop reads, copied once into
+// registers (a descriptor reached through a dynamic index would be reloaded).
+struct CellView {
+    const uint8_t *cls;
+    const void *cells;
+    const void *values;
+    int dim[3];
+    int nb0, nb1;
+    __device__ __forceinline__ explicit CellView(const VolumeDesc &V)
+        : cls(V.brick_class), cells(V.cells), values(V.values), nb0(V.nb[0]), nb1(V.nb[1])
+    {
+        dim[0] = V.dim[0];
+        dim[1] = V.dim[1];
+        dim[2] = V.dim[2];
+    }
+};
+
 // Nearest-voxel psi at voxel-centre coordinates (flag RF_NEAREST): the voxel
 // whose centre is closest, valid if inside the volume and observed.
 template <int DT>
-__device__ __forceinline__ bool sample_nearest_g(const VolumeDesc &V, float gx, float gy, float gz, float &psi)
+__device__ __forceinline__ bool sample_nearest_g(const CellView &V, float gx, float gy, float gz, float &psi)
 {
     using T = typename Storage<DT>::T;
     float f;
     const int ix = floor_split(gx + 0.5f, f), iy = floor_split(gy + 0.5f, f), iz = floor_split(gz + 0.5f, f);
     if (!((unsigned)ix < (unsigned)V.dim[0] && (unsigned)iy < (unsigned)V.dim[1] && (unsigned)iz < (unsigned)V.dim[2]))
         return false;
-    const float v = Storage<DT>::decode(__ldg(&reinterpret_cast<const T *>(V.values)[brick_index(V, ix, iy, iz)]));
+    const size_t brick = (size_t)(ix >> 3) + (size_t)V.nb0 * ((size_t)(iy >> 3) + (size_t)V.nb1 * (size_t)(iz >> 3));
+    const size_t idx = brick * BRICK_VOX + (size_t)((ix & 7) + 8 * ((iy & 7) + 8 * (iz & 7)));
+    const float v = Storage<DT>::decode(__ldg(&reinterpret_cast<const T *>(V.values)[idx]));
     psi = v;
     return !isnan(v);
 }
@@ -254,15 +273,15 @@ template <> struct CellData<RF_F32> {
     float4 a, b;
 };
 
-__device__ __forceinline__ void cell_locate(const VolumeDesc &V, float gx, float gy, float gz, CellRef &c)
+__device__ __forceinline__ void cell_locate(const CellView &V, float gx, float gy, float gz, CellRef &c)
 {
     const int ix = floor_split(gx, c.fx), iy = floor_split(gy, c.fy), iz = floor_split(gz, c.fz);
     const bool inside = (unsigned)ix < (unsigned)(V.dim[0] - 1) && (unsigned)iy < (unsigned)(V.dim[1] - 1) &&
                         (unsigned)iz < (unsigned)(V.dim[2] - 1);
     const unsigned brick =
-        (unsigned)(ix >> 3) + (unsigned)V.nb[0] * ((unsigned)(iy >> 3) + (unsigned)V.nb[1] * (unsigned)(iz >> 3));
+        (unsigned)(ix >> 3) + (unsigned)V.nb0 * ((unsigned)(iy >> 3) + (unsigned)V.nb1 * (unsigned)(iz >> 3));
     c.rec = brick * (unsigned)BRICK_VOX + (unsigned)((ix & 7) | ((iy & 7) << 3) | ((iz & 7) << 6));
-    c.cls = inside ? (unsigned)__ldg(&V.brick_class[brick]) : (unsigned)CELLS_INVALID;
+    c.cls = inside ? (unsigned)__ldg(&V.cls[brick]) : (unsigned)CELLS_INVALID;
 }
 
 // The record of a constant brick is not loaded: the registers get a fill
@@ -275,7 +294,7 @@ __device__ __forceinline__ void ldg_v4_if(bool p, const void *ptr, uint32_t &x, 
         : "r"((int)p), "l"(ptr));
 }
 
-template <int DT> __device__ __forceinline__ void cell_fetch(const VolumeDesc &V, const CellRef &c, CellData<DT> &d)
+template <int DT> __device__ __forceinline__ void cell_fetch(const CellView &V, const CellRef &c, CellData<DT> &d)
 {
     const bool mixed = c.cls == CELLS_MIXED, free_space = c.cls == CELLS_FREE;
     if constexpr (DT == RF_F32) {

@@ -1,0 +1,309 @@
+// fitness.cuh -- device code shared by the standalone fitness kernels (track.cu)
+// and the persistent PFO kernel (pfo.cu): point unprojection, the overlap test of
+// Eq. validness, the warp-level fitness of Eq. normallh over packed TSDF cells, the
+// work split into (particle group, point chunk) units and the per-particle totals.
+#pragma once
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace rf {
+
+
+Pose to_pose(const rf_pose &p);
+
+constexpr int FIT_THREADS = 256;
+constexpr int FIT_WARPS = FIT_THREADS / 32;
+constexpr int CHUNK_MAX = 256;        // points staged per warp (16 B each)
+constexpr int MIN_CHUNK = 32;         // fewest points per work unit
+#ifndef RF_UNITS_PER_WARP
+#define RF_UNITS_PER_WARP 16
+#endif
+constexpr int UNITS_PER_WARP = RF_UNITS_PER_WARP;  // target work units per warp and iteration
+constexpr int APW = 16;               // doubles per CTA in the APS partials
+constexpr int MAX_CTAS_PER_SM = 2048 / FIT_THREADS;  // bound for grid-sized scratch
+// CTAs of the persistent kernel resident per SM (register budget 65536 / (256 * n))
+#ifndef RF_PFO_MIN_BLOCKS
+#define RF_PFO_MIN_BLOCKS 3
+#endif
+
+// ------------------------------------------------------------------ small helpers
+__device__ __forceinline__ long long global_ns()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void unproject_point(const float *__restrict__ depth, const Intr &K, int stride, int nw,
+                                                int j, float4 &out)
+{
+    const int a = j % nw, b = j / nw;
+    const int u = a * stride, v = b * stride;
+    const float z = depth[(size_t)v * K.width + u];
+    if (depth_valid(z, K))
+        out = make_float4(((float)u - K.cx) * z / K.fx, ((float)v - K.cy) * z / K.fy, z, 1.f);
+    else
+        out = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Eq. validness for one point: world with the current estimate (Rc, tc), back
+// into frame t-1 with its final pose (Rp, tp), nearest pixel, valid depth.
+__device__ __forceinline__ bool overlap_test(const float4 &p, const float Rc[9], const float tc[3], const float Rp[9],
+                                             const float tp[3], const float *__restrict__ prev_depth, const Intr &K)
+{
+    if (p.w == 0.f)
+        return false;
+    const float gx = Rc[0] * p.x + Rc[1] * p.y + Rc[2] * p.z + tc[0] - tp[0];
+    const float gy = Rc[3] * p.x + Rc[4] * p.y + Rc[5] * p.z + tc[1] - tp[1];
+    const float gz = Rc[6] * p.x + Rc[7] * p.y + Rc[8] * p.z + tc[2] - tp[2];
+    const float cx = Rp[0] * gx + Rp[3] * gy + Rp[6] * gz;
+    const float cy = Rp[1] * gx + Rp[4] * gy + Rp[7] * gz;
+    const float cz = Rp[2] * gx + Rp[5] * gy + Rp[8] * gz;
+    if (!(cz > 0.f))
+        return false;
+    const float u = floorf(K.fx * cx / cz + K.cx + 0.5f);
+    const float v = floorf(K.fy * cy / cz + K.cy + 0.5f);
+    if (!(u >= 0.f && u < (float)K.width && v >= 0.f && v < (float)K.height))
+        return false;
+    return depth_valid(__ldg(&prev_depth[(size_t)v * K.width + (size_t)u]), K);
+}
+
+// ------------------------------------------------------------------ fitness (warp level)
+// MODE bit 0: nearest sample; bit 1: plain (uncompensated) FP32 sum.
+template <int MODE> struct Mode {
+    static constexpr bool nearest = (MODE & 1) != 0;
+    static constexpr bool plain = (MODE & 2) != 0;
+};
+
+struct FitParams {
+    const float *pst;   // template, structure of arrays with leading dimension ld (pst[d * ld + i])
+    int n;              // particles scored: the first n rows of the template
+    int ld;
+    Pose c;             // PST centre
+    float r[6];         // axis lengths
+    int l1, right_mult;
+};
+
+template <int DT, int MODE, bool L1>
+__device__ __forceinline__ void fitness_points(const CellView &V, const float4 *spts, int cnt, const float R[9],
+                                               float t0, float t1, float t2, float &sum, float &comp, int &nv);
+
+// Lane `lane` of a warp scores particle i over the points staged in `spts`
+// [0, cnt): S = sum psi^2 (|psi| with L1), psi = 1 for invalid samples.
+template <int DT, int MODE>
+__device__ __forceinline__ void fitness_lane(const VolumeDesc &V, const float4 *spts, int cnt, const FitParams &fp,
+                                             int i, double &S_out, int &n_out)
+{
+    Pose P;
+    {
+        const int ii = i < fp.n ? i : 0;
+        float d[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+            d[a] = fp.r[a] * __ldg(&fp.pst[(size_t)a * fp.ld + ii]);
+        compose_offset(fp.c, d, fp.right_mult != 0, P);
+    }
+    // the rotation and translation are folded with the world -> voxel-centre map
+    // g = p / voxel - origin / voxel - 1/2, so a point goes straight to grid units
+    float R[9];
+    quat_rot(P.q, R);
+    const float s = V.inv_voxel;
+    for (int a = 0; a < 9; ++a)
+        R[a] *= s;
+    const float t0 = fmaf(P.t[0], s, V.goff[0]), t1 = fmaf(P.t[1], s, V.goff[1]), t2 = fmaf(P.t[2], s, V.goff[2]);
+    float sum = 0.f, comp = 0.f;
+    int nv = 0;
+    const CellView cv(V);
+    if (fp.l1)
+        fitness_points<DT, MODE, true>(cv, spts, cnt, R, t0, t1, t2, sum, comp, nv);
+    else
+        fitness_points<DT, MODE, false>(cv, spts, cnt, R, t0, t1, t2, sum, comp, nv);
+    S_out = (double)sum + (double)comp;
+    n_out = nv;
+}
+
+// The point loop of one lane: lookups of points [0, cnt) under the grid-space
+// pose (R, t), accumulated as psi^2 (|psi| with L1), psi = 1 when invalid.
+template <int DT, int MODE, bool L1>
+__device__ __forceinline__ void fitness_points(const CellView &V, const float4 *spts, int cnt, const float R[9],
+                                               float t0, float t1, float t2, float &sum, float &comp, int &nv)
+{
+    int j = 0;
+    auto add = [&](float grp) {
+        if (Mode<MODE>::plain)
+            sum += grp;
+        else
+            neumaier_add(sum, comp, grp);
+    };
+    auto term = [&](bool ok, float psi) {
+        nv += ok ? 1 : 0;
+        psi = ok ? psi : 1.f;
+        return L1 ? fabsf(psi) : psi * psi;
+    };
+    if (!Mode<MODE>::nearest) {
+        // groups of 4 lookups: all class loads, then all cell loads, then the
+        // arithmetic, so each group pays the load latency once; a plain FP32
+        // partial of <= 4 terms in [0, 1] is then added with compensation
+        for (; j + 4 <= cnt; j += 4) {
+            CellRef c[4];
+            CellData<DT> d[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 x = spts[j + u];
+                cell_locate(V, fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, t0))),
+                            fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, t1))),
+                            fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, t2))), c[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                cell_fetch<DT>(V, c[u], d[u]);
+            float grp = 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                float psi;
+                const bool ok = cell_eval<DT>(c[u], d[u], psi);
+                grp += term(ok, psi);
+            }
+            add(grp);
+        }
+    }
+    for (; j < cnt; ++j) {  // the tail of the chunk (or every point in nearest mode)
+        const float4 x = spts[j];
+        const float gx = fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, t0)));
+        const float gy = fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, t1)));
+        const float gz = fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, t2)));
+        float psi;
+        bool ok;
+        if (Mode<MODE>::nearest) {
+            ok = sample_nearest_g<DT>(V, gx, gy, gz, psi);
+        } else {
+            CellRef c;
+            CellData<DT> d;
+            cell_locate(V, gx, gy, gz, c);
+            cell_fetch<DT>(V, c, d);
+            ok = cell_eval<DT>(c, d, psi);
+        }
+        add(term(ok, psi));
+    }
+}
+
+// Work decomposition shared by the standalone and the persistent kernels: unit
+// u = (point chunk u / groups, particle group u % groups); consecutive units
+// share a point chunk so the warps of a CTA touch neighbouring voxels.
+struct Split {
+    int groups, n_chunks, chunk;
+};
+
+__host__ __device__ inline Split make_split(int n, int m, int total_warps, int max_chunks)
+{
+    Split s;
+    s.groups = (n + 31) / 32;
+    int want = (UNITS_PER_WARP * total_warps + s.groups - 1) / s.groups;
+    int lo = (m + CHUNK_MAX - 1) / CHUNK_MAX;   // staging capacity
+    int hi = (m + MIN_CHUNK - 1) / MIN_CHUNK;   // at least MIN_CHUNK points per unit
+    want = want < lo ? lo : want;
+    want = want > hi ? hi : want;
+    want = want > max_chunks ? max_chunks : want;
+    want = want < 1 ? 1 : want;
+    s.n_chunks = want;
+    s.chunk = (m + want - 1) / want;
+    if (s.chunk > CHUNK_MAX) {  // only when max_chunks binds
+        s.chunk = CHUNK_MAX;
+        s.n_chunks = (m + CHUNK_MAX - 1) / CHUNK_MAX;
+    }
+    return s;
+}
+
+__host__ inline int max_chunks_for(int n, int m_max, int total_warps)
+{
+    const int groups = (n + 31) / 32;
+    const int a = (UNITS_PER_WARP * total_warps + groups - 1) / groups;
+    const int b = (m_max + CHUNK_MAX - 1) / CHUNK_MAX;
+    return std::max(1, std::max(std::min(a, (m_max + MIN_CHUNK - 1) / MIN_CHUNK), b));
+}
+
+// All warps of the grid walk the units; each stages its chunk of points, scores
+// its 32 particles and writes one (S, n) partial per particle.  `coherent`
+// selects L2-coherent loads for points written earlier in the same kernel.
+// With a unit counter (`next_unit` non-null, zero at the start of the phase) the
+// warps take units dynamically, one atomic per unit, fetched one unit ahead;
+// otherwise warp w takes units w, w + total_warps, ...
+template <int DT, int MODE, bool COHERENT>
+__device__ __forceinline__ void fitness_units(const VolumeDesc &V, const float4 *pts, int m, const FitParams &fp,
+                                              const Split &sp, double *part_S, int *part_n, float4 *smem_pts,
+                                              int warp_global, int total_warps, int lane, int warp_in_block,
+                                              int *next_unit = nullptr)
+{
+    float4 *spts = smem_pts + (size_t)warp_in_block * CHUNK_MAX;
+    const int units = sp.groups * sp.n_chunks;
+    int staged = -1;
+    int u = warp_global;
+    if (next_unit) {
+        int t = 0;
+        if (lane == 0)
+            t = atomicAdd(next_unit, 1);
+        u = __shfl_sync(0xffffffffu, t, 0);
+    }
+    while (u < units) {
+        int u_next = u + total_warps;
+        if (next_unit) {
+            int t = 0;
+            if (lane == 0)
+                t = atomicAdd(next_unit, 1);
+            u_next = __shfl_sync(0xffffffffu, t, 0);
+        }
+        const int ch = u / sp.groups, g = u - ch * sp.groups;
+        const int j0 = ch * sp.chunk;
+        const int cnt = min(sp.chunk, m - j0);
+        if (ch != staged) {
+            __syncwarp();
+            for (int j = lane; j < cnt; j += 32)
+                spts[j] = COHERENT ? __ldcg(&pts[j0 + j]) : __ldg(&pts[j0 + j]);
+            __syncwarp();
+            staged = ch;
+        }
+        const int i = g * 32 + lane;
+        double S;
+        int nv;
+        fitness_lane<DT, MODE>(V, spts, cnt, fp, i, S, nv);
+        if (i < fp.n) {
+            part_S[(size_t)ch * fp.n + i] = S;
+            part_n[(size_t)ch * fp.n + i] = nv;
+        }
+        u = u_next;
+    }
+}
+
+// Fixed-order sum of the chunk partials of particle i, then rho (Eq. normallh,
+// or Eq. ourlh without NORMALIZE).
+__device__ __forceinline__ void particle_total(const double *part_S, const int *part_n, int n, int n_chunks, int i,
+                                               bool coherent, double &S, int &nv)
+{
+    S = 0.0;
+    nv = 0;
+    for (int c = 0; c < n_chunks; ++c) {
+        S += coherent ? __ldcg(&part_S[(size_t)c * n + i]) : part_S[(size_t)c * n + i];
+        nv += coherent ? __ldcg(&part_n[(size_t)c * n + i]) : part_n[(size_t)c * n + i];
+    }
+}
+
+__device__ __forceinline__ float fitness_rho(double S, int nO, float tau, bool normalize)
+{
+    if (nO <= 0)
+        return 0.f;
+    const double x = normalize ? S / ((double)tau * (double)nO) : S / (double)tau;
+    return expf(-(float)x);
+}
+
+
+inline int sm_count()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+}  // namespace rf

@@ -33,7 +33,28 @@ CONFIGS = {
     "precision": dict(dims=512, voxel=0.01, trunc=0.06, dtype="f16", width=640, height=480, stride=4,
                       n_particles=20000, k_max=20, frames=1000, speed=4.0, ang_speed=3.0, noise=True,
                       wall_inset=0.20, seed=0),
+    # Sec. 4 multi-resolution PST: (1024, 1/8), (3072, 1/16), (10240, 1/32) of the pixels in turn,
+    # read as strides 3, 4 and 6 (1/9, 1/16, 1/36 of the pixels)
+    "multires": dict(dims=512, voxel=0.01, trunc=0.06, dtype="i16", width=640, height=480, stride=4,
+                     n_particles=10240, levels=([1024, 3072, 10240], [3, 4, 6]), k_max=20, frames=300,
+                     speed=3.0, ang_speed=3.0, noise=True, wall_inset=0.20, seed=0),
 }
+
+
+def batched_specs(n_seq: int = 16, seed: int = 0):
+    """Uneven sequences stepped together: depth 80x60 .. 320x240, TSDF 256^3 .. 512^3
+    over the same 5.12 m room extent, 10k .. 40k particles, int16 storage."""
+    rng = np.random.default_rng(30_000 + seed)
+    sizes = [(80, 60), (160, 120), (240, 180), (320, 240)]
+    specs = []
+    for i in range(n_seq):
+        w, h = sizes[int(rng.integers(0, len(sizes)))]
+        dims = int(rng.choice([256, 384, 512]))
+        voxel = 5.12 / dims
+        specs.append(dict(dims=dims, voxel=voxel, trunc=6 * voxel, dtype="i16", width=w, height=h, stride=1,
+                          n_particles=int(rng.integers(10_000, 40_001)), k_max=20, speed=3.0, ang_speed=3.0,
+                          noise=True, wall_inset=0.20, seed=seed + i))
+    return specs
 
 
 def intrinsics(width: int, height: int, z_min: float = 0.1, z_max: float = 8.0) -> dict:

@@ -1,0 +1,116 @@
+"""Storage precision (FP32 / FP16 / int16 TSDF, FP32 arithmetic) against the FP64
+oracle on UNROUNDED values: the same analytic room TSDF is given to the oracle
+in FP64 and to the GPU rounded to its storage type, so the measured gap is the
+whole precision budget of the path (storage rounding + FP32 pose composition,
+interpolation and accumulation).  Reported per storage type: the relative error
+of per-particle fitness and the pose error of one tracked frame.  When the
+environment variable RF_PRECISION_REPORT names a file, the numbers are written
+there as JSON."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from gpu_common import pose_f32
+from paper_2105_05600_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+# relative fitness error bounds derived from the storage step: float32 ~6e-8
+# (FP32 arithmetic dominates: the parity bar), half 2^-11 = 4.9e-4 per value,
+# int16 1/32767 = 3.1e-5 per value (psi^2 errors partly cancel over the points)
+FIT_BOUND = {"f32": 1e-4, "f16": 2e-3, "i16": 5e-4}
+_REPORT = {}
+
+
+@pytest.fixture(scope="module")
+def nat():
+    from paper_2105_05600_gb300 import build
+
+    build.build()
+    from paper_2105_05600_gb300 import _native
+
+    return _native
+
+
+@pytest.fixture(scope="module")
+def room(oracle):
+    dims, voxel, trunc = 256, 0.02, 0.12
+    scene = synth.make_scene(dims * voxel, 0.2, 4)
+    # fully observed: no validity edges inside the volume, so the measured gap is
+    # the precision of storage and arithmetic alone
+    F = synth.analytic_tsdf(scene.sdf, (dims,) * 3, voxel, (0, 0, 0), trunc)
+    ov = oracle.Volume((dims,) * 3, voxel, (0, 0, 0), trunc)
+    ov.F[:] = F.reshape(-1)
+    traj = synth.make_trajectory(scene, 2, 3.0, 3.0, 4)
+    K = synth.intrinsics(320, 240)
+    rng = np.random.default_rng(8)
+    d0 = synth.render_depth(scene, traj[0], K, rng)
+    d1 = synth.render_depth(scene, traj[1], K, rng)
+    return dict(dims=dims, voxel=voxel, trunc=trunc, F=F, ov=ov, traj=traj, K=K, d0=d0, d1=d1)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "i16"])
+def test_fitness_error_vs_fp64(oracle, nat, room, dtype):
+    import torch
+
+    gv = nat.Volume(room["dims"], room["voxel"], room["trunc"], (0, 0, 0), dtype)
+    gv.upload(synth.encode_values(room["F"], dtype))
+    pts = oracle.unproject(room["d1"], room["K"], 2)
+    pts = pts[pts[:, 3] > 0].astype(np.float32).astype(np.float64)
+    n = 4096
+    pst = nat.pst_create(n, seed=1)
+    centre = pose_f32(room["traj"][0])
+    scale = pose_f32([0.02] * 3 + [0.04] * 3)[:6]
+    rho, S, nv = nat.fitness_eval(gv, torch.from_numpy(pts.astype(np.float32)).cuda(), pst, centre, scale,
+                                  nat.make_params())
+    rho, S = rho.cpu().numpy(), S.cpu().numpy()
+    ones = np.ones(len(pts), np.int32)
+    rel, rel_rho, flips = [], [], 0
+    for i in np.random.default_rng(2).choice(n, 32, replace=False):
+        pose = oracle.particle_pose(centre, scale, pst[:, i].cpu().numpy().astype(np.float64))
+        So, no, _, rho_o, fr = room["ov"].fitness_fragile(pts, ones, pose)
+        flips += fr  # only the volume's outer faces can flip a sample here
+        assert abs(S[i] - So) <= FIT_BOUND[dtype] * So + fr
+        rel.append(abs(S[i] - So) / So)
+        rel_rho.append(abs(rho[i] - rho_o) / rho_o)
+    rel, rel_rho = np.array(rel), np.array(rel_rho)
+    _REPORT.setdefault(dtype, {})["fitness_rel_err"] = {"S_max": float(rel.max()), "S_mean": float(rel.mean()),
+                                                        "rho_max": float(rel_rho.max()), "particles": int(len(rel)),
+                                                        "fragile_samples": int(flips)}
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "i16"])
+def test_pose_error_vs_fp64(oracle, nat, room, dtype):
+    import torch
+
+    gv = nat.Volume(room["dims"], room["voxel"], room["trunc"], (0, 0, 0), dtype)
+    gv.upload(synth.encode_values(room["F"], dtype))
+    n, k_max = 2048, 12
+    pst = nat.pst_create(n, seed=1)
+    tr = nat.Tracker(gv, pst, nat.make_params(k_max=k_max, stride=4), 320, 240)
+    tr.set_scale([0.05] * 6)
+    prev = pose_f32(room["traj"][0])
+    pose, st, status = nat.pfo_track_frame(tr, torch.from_numpy(room["d1"]).cuda(),
+                                           torch.from_numpy(room["d0"]).cuda(), room["K"], prev)
+    assert status == 0
+    pts = oracle.unproject(room["d1"], room["K"], 4)
+    res = room["ov"].pfo_frame(pts, room["d0"], room["K"], prev, prev, np.full(6, np.float32(0.05)),
+                               oracle.pst_uniform(n, 1), dict(tau=1.0, beta=0.1, eps=1e-3, stop_eps=1e-6,
+                                                              k_max=k_max, flags=oracle.DEFAULT_FLAGS))
+    dt = float(np.linalg.norm(pose[4:] - res["pose"][4:]))
+    # angle of the relative rotation, 2 atan2(|v|, |w|) of q_gpu^-1 q_oracle (stable near 0)
+    rel = oracle.quat_mul(pose[:4] * np.array([1, -1, -1, -1]) / np.linalg.norm(pose[:4]), res["pose"][:4])
+    dr = math.degrees(2 * math.atan2(float(np.linalg.norm(rel[1:])), abs(float(rel[0]))))
+    gt = room["traj"][1]
+    _REPORT.setdefault(dtype, {})["pose_vs_fp64"] = {"translation_m": dt, "rotation_deg": dr,
+                                                     "gpu_error_to_truth_m": float(np.linalg.norm(pose[4:] - gt[4:])),
+                                                     "oracle_error_to_truth_m": float(
+                                                         np.linalg.norm(res["pose"][4:] - gt[4:]))}
+    path = os.environ.get("RF_PRECISION_REPORT")
+    if path:
+        with open(path, "w") as f:
+            json.dump(_REPORT, f, indent=1)
+    assert dt < 0.02 and dr < 1.0

@@ -302,6 +302,30 @@ rf_status pfo_track_frame_async(rf_tracker tr, const float *depth_dev, const flo
                                 const rf_intrinsics *K, const float *prev_pose_dev, float *out_pose_dev,
                                 rf_frame_stats *stats_dev, void *stream);
 /*
+ * pfo_track_frame_ex_async -- pfo_track_frame_async with the Sec. 4 PST
+ * initialisation supplied by the caller (e.g. a learned proposal):
+ *   init_pose_dev  device float[7]: the swarm centre c_0 (NULL: prev_pose_dev).
+ *                  prev_pose_dev stays the pose of frame t-1 for the overlap set.
+ *   scale_dev      device float[6]: r_0 in, r_1 of this frame out (NULL: the
+ *                  tracker's own r_0 / r_1 buffer)
+ *   run_flag_dev   device int (may be NULL): read when the kernel starts; zero
+ *                  means the frame is skipped (no iteration; out_pose_dev and
+ *                  scale_dev untouched, stats_dev zeroed).  Lets a conditional
+ *                  second run sit in a stream or CUDA graph.
+ *   k_max          > 0: iteration cap of this call (<= RF_MAX_ITERS); 0: the
+ *                  tracker's
+ */
+typedef struct {
+    const float *init_pose_dev;
+    float *scale_dev;
+    const int *run_flag_dev;
+    int k_max;
+    int reserved;
+} rf_track_options;
+rf_status pfo_track_frame_ex_async(rf_tracker tr, const float *depth_dev, const float *prev_depth_dev,
+                                   const rf_intrinsics *K, const float *prev_pose_dev, float *out_pose_dev,
+                                   rf_frame_stats *stats_dev, const rf_track_options *opt, void *stream);
+/*
  * pfo_track_frame -- pfo_track_frame_async with host poses: copies
  * prev_pose in, runs, synchronises the stream and writes out_pose (host) and
  * stats_host (may be NULL).  Returns the frame's device status.

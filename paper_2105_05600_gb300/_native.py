@@ -1,4 +1,4 @@
-"""ctypes binding of librosefusion.so (include/rosefusion.h).
+"""ctypes binding of librosefusion.so (include/rosefusion.h, include/rf_proposal.h).
 
 Argument marshalling only: every function here has the name of the C entry
 point it calls, turns torch tensors into device pointers and numpy arrays into
@@ -63,6 +63,26 @@ class rf_frame_stats(ctypes.Structure):
                 ("pad", ctypes.c_float * 2), ("it", rf_iter_stats * RF_MAX_ITERS)]
 
 
+class rf_track_options(ctypes.Structure):
+    _fields_ = [("init_pose_dev", ctypes.c_void_p), ("scale_dev", ctypes.c_void_p), ("run_flag_dev", ctypes.c_void_p),
+                ("k_max", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class rf_proposal_params(ctypes.Structure):
+    _fields_ = [("k_learned", ctypes.c_int), ("k_fallback", ctypes.c_int), ("kappa", ctypes.c_float),
+                ("theta", ctypes.c_float), ("r_min", ctypes.c_float * 6), ("r_max", ctypes.c_float * 6)]
+
+
+class rf_learned_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("used_fallback", ctypes.c_int), ("chose_fallback", ctypes.c_int),
+                ("iters_learned", ctypes.c_int), ("iters_fallback", ctypes.c_int), ("rho_learned", ctypes.c_float),
+                ("rho_fallback", ctypes.c_float), ("rho_prev", ctypes.c_float), ("init_pose", ctypes.c_float * 7),
+                ("r0", ctypes.c_float * 6), ("lookups", ctypes.c_longlong)]
+
+
+RF_MLP_IN, RF_MLP_IN_USED, RF_MLP_HIDDEN, RF_MLP_OUT, RF_MLP_OUT_USED = 832, 774, 256, 16, 12
+RF_MLP_MAX_BATCH, RF_MLP_MAX_TRAIN_BATCH = 4096, 1024
+
 EXPORTS = ["rf_last_error", "rf_version", "pst_create", "rf_volume_create", "rf_volume_destroy", "rf_volume_reset",
            "rf_volume_upload", "rf_volume_download", "rf_volume_info", "tsdf_integrate", "tsdf_integrate_dev",
            "rf_depth_to_points",
@@ -71,7 +91,11 @@ EXPORTS = ["rf_last_error", "rf_version", "pst_create", "rf_volume_create", "rf_
            "pfo_track_frame", "rf_tracker_last_status", "rf_sequence_start", "rf_sequence_step",
            "rf_tracker_debug_skip_barrier", "rf_batch_create", "rf_batch_destroy", "rf_batch_depth_slot",
            "rf_batch_pose_dev", "rf_batch_start", "rf_batch_step", "rf_batch_autotune", "rf_batch_set_config",
-           "rf_batch_stats_dev"]
+           "rf_batch_stats_dev", "pfo_track_frame_ex_async", "rf_mlp_num_params", "rf_mlp_create",
+           "rf_mlp_destroy", "rf_mlp_set_params", "rf_mlp_get_params", "rf_mlp_forward", "rf_mlp_gradient",
+           "rf_mlp_train_step", "rf_mlp_status", "rf_proposal_features", "rf_proposal_target",
+           "rf_proposal_default_params", "rf_proposal_apply", "rf_learned_create", "rf_learned_destroy",
+           "rf_learned_start", "rf_learned_step"]
 
 
 def _load():
@@ -121,6 +145,25 @@ def _load():
         "rf_batch_autotune": (i, [P, i, ctypes.POINTER(rf_launch_config), P]),
         "rf_batch_set_config": (i, [P, ctypes.POINTER(rf_launch_config)]),
         "rf_batch_stats_dev": (i, [P, ctypes.POINTER(P)]),
+        "pfo_track_frame_ex_async": (i, [P, P, P, ctypes.POINTER(rf_intrinsics), P, P, P,
+                                         ctypes.POINTER(rf_track_options), P]),
+        "rf_mlp_num_params": (i, []),
+        "rf_mlp_create": (i, [i, ctypes.POINTER(P)]),
+        "rf_mlp_destroy": (None, [P]),
+        "rf_mlp_set_params": (i, [P, ctypes.POINTER(f)]),
+        "rf_mlp_get_params": (i, [P, ctypes.POINTER(f)]),
+        "rf_mlp_forward": (i, [P, P, i, P, P]),
+        "rf_mlp_gradient": (i, [P, P, P, P, i, i, P, P, P, P]),
+        "rf_mlp_train_step": (i, [P, P, P, P, i, i, f, P, P]),
+        "rf_mlp_status": (i, [P]),
+        "rf_proposal_features": (i, [P, P, ctypes.POINTER(rf_intrinsics), P, P, P, P]),
+        "rf_proposal_target": (i, [P, P, P, P]),
+        "rf_proposal_default_params": (None, [ctypes.POINTER(rf_proposal_params)]),
+        "rf_proposal_apply": (i, [P, P, ctypes.POINTER(rf_proposal_params), P, P, P]),
+        "rf_learned_create": (i, [P, P, P, ctypes.POINTER(rf_proposal_params), i, i, ctypes.POINTER(P)]),
+        "rf_learned_destroy": (None, [P]),
+        "rf_learned_start": (i, [P, P, i, ctypes.POINTER(rf_intrinsics), ctypes.POINTER(rf_pose), P]),
+        "rf_learned_step": (i, [P, P, i, ctypes.POINTER(rf_intrinsics), i, ctypes.POINTER(rf_pose), P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -527,3 +570,188 @@ def _any_ptr(a):
     if not a.is_contiguous():
         raise ValueError("expected a contiguous tensor")
     return ctypes.c_void_p(a.data_ptr()), 1
+
+
+def pfo_track_frame_ex_async(tr: Tracker, depth, prev_depth, K: dict, prev_pose_dev, out_pose_dev, stats_dev=None,
+                             init_pose_dev=None, scale_dev=None, run_flag_dev=None, k_max=0, stream=None):
+    """pfo_track_frame_async with a caller-supplied c_0 / r_0, run flag and iteration cap."""
+    import torch
+
+    Ki = make_intrinsics(K)
+    o = rf_track_options(_dptr(init_pose_dev, torch.float32), _dptr(scale_dev, torch.float32),
+                         _dptr(run_flag_dev, torch.int32), int(k_max), 0)
+    _check(lib.pfo_track_frame_ex_async(tr.handle, _dptr(depth, torch.float32), _dptr(prev_depth, torch.float32),
+                                        ctypes.byref(Ki), _dptr(prev_pose_dev, torch.float32),
+                                        _dptr(out_pose_dev, torch.float32), _dptr(stats_dev), ctypes.byref(o),
+                                        _stream(stream)))
+
+
+# --------------------------------------------------------------------------- learned proposal (rf_proposal.h)
+def _bf16_ptr(t):
+    """Device pointer of a contiguous bfloat16 (or int16 bit-pattern) CUDA tensor."""
+    import torch
+
+    if t.dtype not in (torch.bfloat16, torch.int16):
+        raise ValueError(f"expected bfloat16 bits, got {t.dtype}")
+    return _dptr(t)
+
+
+def rf_mlp_num_params() -> int:
+    return int(lib.rf_mlp_num_params())
+
+
+class MLP:
+    """rf_mlp: the proposal network's parameters, Adam state and activations on the device."""
+
+    def __init__(self, max_batch: int):
+        h = ctypes.c_void_p()
+        _check(lib.rf_mlp_create(int(max_batch), ctypes.byref(h)))
+        self.handle = h
+        self.max_batch = int(max_batch)
+        self.n_params = rf_mlp_num_params()
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            lib.rf_mlp_destroy(h)
+            self.handle = None
+
+    def set_params(self, theta):
+        a = np.ascontiguousarray(theta, dtype=np.float32).reshape(-1)
+        if a.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {a.size}")
+        _check(lib.rf_mlp_set_params(self.handle, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def get_params(self) -> np.ndarray:
+        a = np.zeros(self.n_params, dtype=np.float32)
+        _check(lib.rf_mlp_get_params(self.handle, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return a
+
+    def forward(self, x, out=None, stream=None):
+        """x: (B, 832) bfloat16 CUDA tensor -> (B, 16) float32."""
+        import torch
+
+        B = x.shape[0]
+        if out is None:
+            out = torch.empty((B, RF_MLP_OUT), dtype=torch.float32, device="cuda")
+        _check(lib.rf_mlp_forward(self.handle, _bf16_ptr(x), int(B), _dptr(out, torch.float32), _stream(stream)))
+        return out
+
+    def gradient(self, x_all, y_all, batch, idx=None, stream=None):
+        """(grad float32[P], loss float32[1], outputs float32[batch, 16]) of one batch."""
+        import torch
+
+        grad = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        out = torch.empty((batch, RF_MLP_OUT), dtype=torch.float32, device="cuda")
+        _check(lib.rf_mlp_gradient(self.handle, _bf16_ptr(x_all), _dptr(y_all, torch.float32),
+                                   _dptr(idx, torch.int32), int(x_all.shape[0]), int(batch), _dptr(grad),
+                                   _dptr(loss), _dptr(out), _stream(stream)))
+        return grad, loss, out
+
+    def train_step(self, x_all, y_all, batch, lr, idx=None, loss_out=None, stream=None):
+        import torch
+
+        _check(lib.rf_mlp_train_step(self.handle, _bf16_ptr(x_all), _dptr(y_all, torch.float32),
+                                     _dptr(idx, torch.int32), int(x_all.shape[0]), int(batch), float(lr),
+                                     _dptr(loss_out, torch.float32), _stream(stream)))
+
+    def status(self) -> int:
+        return lib.rf_mlp_status(self.handle)
+
+
+def rf_proposal_features(depth, prev_depth, K: dict, pose_prev2_dev, pose_prev_dev, x_out=None, stream=None):
+    """Network input of one frame pair -> bfloat16 CUDA tensor [832] (or x_out, a row of a dataset)."""
+    import torch
+
+    if x_out is None:
+        x_out = torch.empty(RF_MLP_IN, dtype=torch.bfloat16, device="cuda")
+    Ki = make_intrinsics(K)
+    _check(lib.rf_proposal_features(_dptr(depth, torch.float32), _dptr(prev_depth, torch.float32), ctypes.byref(Ki),
+                                    _dptr(pose_prev2_dev, torch.float32), _dptr(pose_prev_dev, torch.float32),
+                                    _bf16_ptr(x_out), _stream(stream)))
+    return x_out
+
+
+def rf_proposal_target(pose_prev_dev, pose_cur_dev, y_out=None, stream=None):
+    import torch
+
+    if y_out is None:
+        y_out = torch.empty(6, dtype=torch.float32, device="cuda")
+    _check(lib.rf_proposal_target(_dptr(pose_prev_dev, torch.float32), _dptr(pose_cur_dev, torch.float32),
+                                  _dptr(y_out, torch.float32), _stream(stream)))
+    return y_out
+
+
+def proposal_params(**kw) -> rf_proposal_params:
+    p = rf_proposal_params()
+    lib.rf_proposal_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k in ("r_min", "r_max"):
+            setattr(p, k, (ctypes.c_float * 6)(*v))
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def rf_proposal_apply(out_dev, pose_prev_dev, params: rf_proposal_params, stream=None):
+    """(c_0 float32[7], r_0 float32[6]) CUDA tensors from one network output."""
+    import torch
+
+    c0 = torch.empty(7, dtype=torch.float32, device="cuda")
+    r0 = torch.empty(6, dtype=torch.float32, device="cuda")
+    _check(lib.rf_proposal_apply(_dptr(out_dev, torch.float32), _dptr(pose_prev_dev, torch.float32),
+                                 ctypes.byref(params), _dptr(c0), _dptr(r0), _stream(stream)))
+    return c0, r0
+
+
+def learned_stats_dict(t) -> dict:
+    raw = t.cpu().numpy().tobytes()[:ctypes.sizeof(rf_learned_stats)]
+    s = rf_learned_stats.from_buffer_copy(raw)
+    return dict(status=s.status, used_fallback=s.used_fallback, chose_fallback=s.chose_fallback,
+                iters_learned=s.iters_learned, iters_fallback=s.iters_fallback, rho_learned=s.rho_learned,
+                rho_fallback=s.rho_fallback, rho_prev=s.rho_prev, init_pose=list(s.init_pose), r0=list(s.r0),
+                lookups=s.lookups)
+
+
+def new_learned_stats_buffer(device="cuda"):
+    import torch
+
+    return torch.zeros(ctypes.sizeof(rf_learned_stats), dtype=torch.uint8, device=device)
+
+
+class Learned:
+    """rf_learned: proposal-driven tracking of one sequence (tracker + volume + trained network)."""
+
+    def __init__(self, tr: Tracker, vol: Volume, net: MLP, params: rf_proposal_params, max_width: int,
+                 max_height: int):
+        h = ctypes.c_void_p()
+        _check(lib.rf_learned_create(tr.handle, vol.handle, net.handle, ctypes.byref(params), int(max_width),
+                                     int(max_height), ctypes.byref(h)))
+        self.handle = h
+        self._keep = (tr, vol, net)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            lib.rf_learned_destroy(h)
+            self.handle = None
+
+    def start(self, depth, K: dict, pose, stream=None):
+        Ki = make_intrinsics(K)
+        P = make_pose(pose)
+        ptr, on_host = _any_ptr(depth)
+        _check(lib.rf_learned_start(self.handle, ptr, on_host, ctypes.byref(Ki), ctypes.byref(P), _stream(stream)))
+
+    def step(self, depth, K: dict, use_graph=False, want_host_pose=True, out_pose_dev=None, stats_dev=None,
+             stream=None):
+        """Track + fuse the next frame.  Returns (pose float64[7] or None, status)."""
+        Ki = make_intrinsics(K)
+        ptr, on_host = _any_ptr(depth)
+        out = rf_pose() if want_host_pose else None
+        status = lib.rf_learned_step(self.handle, ptr, on_host, ctypes.byref(Ki), int(bool(use_graph)),
+                                     ctypes.byref(out) if out is not None else None, _dptr(out_pose_dev),
+                                     _dptr(stats_dev), _stream(stream))
+        if status < 0 and status != RF_ERR_EMPTY:
+            _check(status)
+        return (pose_array(out) if out is not None else None), status

@@ -46,6 +46,8 @@ struct ProblemDesc {
     int lvl_n[MAX_LEVELS], lvl_stride[MAX_LEVELS], lvl_nw[MAX_LEVELS], lvl_m[MAX_LEVELS], lvl_off[MAX_LEVELS];
     int m_all;  // points of all levels (concatenated in pts at lvl_off)
     const float *prev_pose;
+    const float *init_pose;  // c_0 (NULL: prev_pose)
+    const int *run_flag;     // NULL, or skip the frame when *run_flag == 0 at launch
     float *out_pose;
     rf_frame_stats *stats;
     float *scale;  // r_0 in, r_1 out
@@ -217,16 +219,22 @@ __global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kern
     if (tid < B) {
         const ProblemDesc &pd = P.prob[tid];
         PState &s = st[tid];
-        for (int a = 0; a < 4; ++a)
-            s.c.q[a] = s.prev.q[a] = __ldcg(&pd.prev_pose[a]);
-        for (int a = 0; a < 3; ++a)
-            s.c.t[a] = s.prev.t[a] = __ldcg(&pd.prev_pose[4 + a]);
+        const float *c0 = pd.init_pose ? pd.init_pose : pd.prev_pose;
+        for (int a = 0; a < 4; ++a) {
+            s.c.q[a] = __ldcg(&c0[a]);
+            s.prev.q[a] = __ldcg(&pd.prev_pose[a]);
+        }
+        for (int a = 0; a < 3; ++a) {
+            s.c.t[a] = __ldcg(&c0[4 + a]);
+            s.prev.t[a] = __ldcg(&pd.prev_pose[4 + a]);
+        }
         for (int d = 0; d < 6; ++d)
             s.r[d] = s.r1[d] = __ldcg(&pd.scale[d]);
         s.rho_carry = 0.f;
         s.rho_ref = 0.f;
         s.empty_run = 0;
-        s.stop = 0;
+        // stop code 5: skipped by the caller's run flag (never active, writes nothing)
+        s.stop = (pd.run_flag && __ldcg(pd.run_flag) == 0) ? 5 : 0;
         s.iters = 0;
         s.lookups = 0;
     }
@@ -611,7 +619,7 @@ __global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kern
         __syncthreads();
     }
     // ---- epilogue (CTA 0): final poses, r_1 for the next frame, summaries
-    if (b == 0 && tid < B) {
+    if (b == 0 && tid < B && st[tid].stop != 5) {
         const ProblemDesc &pd = P.prob[tid];
         const PState &s = st[tid];
         for (int a = 0; a < 4; ++a)
@@ -1023,6 +1031,31 @@ rf_status pfo_track_frame_async(rf_tracker tr, const float *depth_dev, const flo
         tr->timeout_ns = 1000000000ll;
     }
     return RF_OK;
+}
+
+rf_status pfo_track_frame_ex_async(rf_tracker tr, const float *depth_dev, const float *prev_depth_dev,
+                                   const rf_intrinsics *K, const float *prev_pose_dev, float *out_pose_dev,
+                                   rf_frame_stats *stats_dev, const rf_track_options *opt, void *stream)
+{
+    RF_CHECK_ARG(tr && depth_dev && prev_depth_dev && K && prev_pose_dev && out_pose_dev && opt, "null pointer");
+    RF_CHECK_ARG(opt->k_max >= 0 && opt->k_max <= RF_MAX_ITERS, "k_max outside [0, RF_MAX_ITERS]");
+    cudaStream_t s = (cudaStream_t)stream;
+    BatchParams P;
+    memset(&P, 0, sizeof P);
+    rf_status st = fill_problem(tr, depth_dev, prev_depth_dev, K, prev_pose_dev, out_pose_dev, stats_dev, P.prob[0]);
+    if (st != RF_OK)
+        return st;
+    ProblemDesc &pd = P.prob[0];
+    pd.init_pose = opt->init_pose_dev;
+    pd.run_flag = opt->run_flag_dev;
+    if (opt->scale_dev)
+        pd.scale = opt->scale_dev;
+    if (opt->k_max > 0)
+        pd.k_max = opt->k_max;
+    P.B = 1;
+    P.work_warps = WORK_WARPS_DEFAULT;
+    P.timeout_ns = tr->timeout_ns;
+    return launch_batch(P, tr->ls, tr->vol->d.dtype, mode_of(tr->p.flags), 0, 0, s);
 }
 
 rf_status pfo_track_frame(rf_tracker tr, const float *depth_dev, const float *prev_depth_dev, const rf_intrinsics *K,

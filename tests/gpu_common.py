@@ -50,3 +50,27 @@ def to_gpu_points(pts):
 def pose_f32(p):
     """A pose as the GPU holds it (float32), back in float64 for the oracle."""
     return np.asarray(p, np.float64).astype(np.float32).astype(np.float64)
+
+
+def compare_traces(gst, otr, n_pts_margin=None):
+    """Compare GPU stats rows with oracle trace rows; returns #iterations compared strictly."""
+    strict = 0
+    for k, (g, o) in enumerate(zip(gst["it"], otr)):
+        ambiguous_overlap = o[27] < 1e-3
+        ambiguous_aps = o[26] < 1e-5
+        if not ambiguous_overlap:
+            assert g["n_overlap"] == int(o[1]), (k, g["n_overlap"], o[1])
+        else:
+            assert abs(g["n_overlap"] - int(o[1])) <= 3
+        if ambiguous_overlap or ambiguous_aps:
+            break
+        assert g["n_aps"] == int(o[2]), (k, g["n_aps"], o[2])
+        assert abs(g["rho_ref"] - o[3]) <= 1e-4 * o[3]
+        assert abs(g["rho_tilde"] - o[4]) <= 1e-4 * o[4]
+        gp, op = np.array(g["pose"]), o[7:14]
+        if np.dot(gp[:4], op[:4]) < 0:
+            gp[:4] = -gp[:4]
+        np.testing.assert_allclose(gp, op, atol=2e-4)
+        np.testing.assert_allclose(g["scale"], o[14:20], rtol=2e-3, atol=2e-6)
+        strict += 1
+    return strict

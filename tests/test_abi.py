@@ -9,24 +9,30 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "rosefusion.h")
+INCLUDE = os.path.join(ROOT, "include")
+HEADERS = sorted(os.path.join(INCLUDE, h) for h in os.listdir(INCLUDE) if h.endswith(".h"))
 
 
 def declared_functions():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:rf_status|void|const char\s*\*)\s*\*?\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(", src, re.M)
+    names = []
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:rf_status|void|int|const char\s*\*)\s*\*?\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                            src, re.M)
     return sorted(set(names))
 
 
-def test_header_is_plain_c():
+@pytest.mark.parametrize("header", HEADERS)
+def test_header_is_plain_c(header):
     # no CUDA, torch or C++ types in the signatures: a C compiler accepts it alone
-    subprocess.check_call(["gcc", "-fsyntax-only", "-std=c99", "-Wall", "-Werror", "-x", "c", HEADER])
+    subprocess.check_call(["gcc", "-fsyntax-only", "-std=c99", "-Wall", "-Werror", "-I", INCLUDE, "-x", "c", header])
 
 
 def test_header_declares_the_entry_points():
     names = declared_functions()
-    for must in ("pst_create", "tsdf_integrate", "fitness_eval", "pfo_track_frame"):
+    for must in ("pst_create", "tsdf_integrate", "fitness_eval", "pfo_track_frame", "rf_mlp_train_step",
+                 "rf_learned_step"):
         assert must in names
 
 
@@ -56,9 +62,10 @@ def test_structs_match_the_header(built_lib):
 
     probe = r"""
 #include <stdio.h>
-#include "rosefusion.h"
-int main(void) { printf("%zu %zu %zu %zu %zu\n", sizeof(rf_intrinsics), sizeof(rf_pose), sizeof(rf_params),
-                        sizeof(rf_iter_stats), sizeof(rf_frame_stats)); return 0; }
+#include "rf_proposal.h"
+int main(void) { printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rf_intrinsics), sizeof(rf_pose),
+                        sizeof(rf_params), sizeof(rf_iter_stats), sizeof(rf_frame_stats), sizeof(rf_track_options),
+                        sizeof(rf_proposal_params), sizeof(rf_learned_stats)); return 0; }
 """
     import tempfile
 
@@ -69,7 +76,8 @@ int main(void) { printf("%zu %zu %zu %zu %zu\n", sizeof(rf_intrinsics), sizeof(r
         subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         sizes = [int(x) for x in subprocess.check_output([exe]).split()]
     mine = [ctypes.sizeof(t) for t in (_native.rf_intrinsics, _native.rf_pose, _native.rf_params,
-                                       _native.rf_iter_stats, _native.rf_frame_stats)]
+                                       _native.rf_iter_stats, _native.rf_frame_stats, _native.rf_track_options,
+                                       _native.rf_proposal_params, _native.rf_learned_stats)]
     assert sizes == mine
 
 
@@ -84,3 +92,22 @@ def test_argument_errors_need_no_gpu(built_lib):
     assert n.lib.rf_volume_create(12, 16, 16, 0.01, 0.03, org, 0, ctypes.byref(h)) == n.RF_ERR_ARG
     assert n.lib.fitness_eval(None, None, 0, None, 0, None, None, None, None, None, None, None) == n.RF_ERR_ARG
     assert n.lib.rf_tracker_create(None, None, 0, None, 0, 0, ctypes.byref(h)) == n.RF_ERR_ARG
+
+
+def test_proposal_argument_errors_need_no_gpu(built_lib):
+    from paper_2105_05600_gb300 import _native as n
+
+    h = ctypes.c_void_p()
+    assert n.lib.rf_mlp_num_params() == 348944
+    assert n.lib.rf_mlp_create(0, ctypes.byref(h)) == n.RF_ERR_ARG
+    assert n.lib.rf_mlp_create(n.RF_MLP_MAX_BATCH + 1, ctypes.byref(h)) == n.RF_ERR_ARG
+    assert n.lib.rf_mlp_forward(None, None, 1, None, None) == n.RF_ERR_ARG
+    assert n.lib.rf_mlp_train_step(None, None, None, None, 8, 8, 1e-3, None, None) == n.RF_ERR_ARG
+    p = n.proposal_params()
+    assert (p.k_learned, p.k_fallback) == (5, 20) and abs(p.kappa - 2.0) < 1e-7 and abs(p.theta - 0.9) < 1e-7
+    assert n.lib.rf_proposal_apply(None, None, ctypes.byref(p), None, None, None) == n.RF_ERR_ARG
+    bad = n.proposal_params(k_learned=0)
+    assert n.lib.rf_learned_create(None, None, None, ctypes.byref(bad), 8, 8, ctypes.byref(h)) == n.RF_ERR_ARG
+    o = n.rf_track_options(None, None, None, n.RF_MAX_ITERS + 1, 0)
+    assert n.lib.pfo_track_frame_ex_async(None, None, None, None, None, None, None, ctypes.byref(o),
+                                          None) == n.RF_ERR_ARG

@@ -1,0 +1,195 @@
+"""Proposal-driven tracking through the C ABI: the extended frame call (a swarm
+centre c_0 apart from the previous pose, caller-held axis lengths, iteration
+cap, run flag) against the FP64 oracle's Algorithm 1 with the same
+initialisation, and the learned driver (rf_learned_step): its proposal, its
+short PFO run and its fallback rule.  Trace parity bar as in
+test_gpu_tracker.py."""
+import numpy as np
+import pytest
+
+from gpu_common import analytic_volume_codes, compare_traces, oracle_volume, pose_f32
+from oracle import mlp
+from paper_2105_05600_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nat():
+    from paper_2105_05600_gb300 import build
+
+    build.build()
+    from paper_2105_05600_gb300 import _native
+
+    return _native
+
+
+def oracle_params(oracle, k_max, flags=None):
+    return dict(tau=1.0, beta=0.1, eps=1e-3, stop_eps=1e-6, k_max=k_max,
+                flags=oracle.DEFAULT_FLAGS if flags is None else flags)
+
+
+@pytest.fixture(scope="module")
+def tiny(oracle, nat):
+    scene, codes, F64, cfg = analytic_volume_codes("tiny", dtype="f32")
+    traj = synth.make_trajectory(scene, 6, cfg["speed"], cfg["ang_speed"], cfg["seed"])
+    K = synth.intrinsics(cfg["width"], cfg["height"])
+    depths = [synth.render_depth(scene, p, K) for p in traj]
+    return dict(scene=scene, codes=codes, F64=F64, cfg=cfg, traj=traj, K=K, depths=depths,
+                ov=oracle_volume(oracle, cfg, F64))
+
+
+def gpu_volume(nat, tiny):
+    cfg = tiny["cfg"]
+    gv = nat.Volume(cfg["dims"], cfg["voxel"], cfg["trunc"], (0, 0, 0), cfg["dtype"])
+    gv.upload(tiny["codes"])
+    return gv
+
+
+def test_ex_async_with_a_separate_centre(oracle, nat, tiny):
+    # With c_0 != s*_{t-1} the overlap test of iteration 1 already projects to
+    # generic sub-pixel positions, where a rounding boundary within the parity
+    # margin is likely; the trace is compared with the overlap test off (every
+    # valid point scored), where no pixel rounding takes a decision.
+    import torch
+
+    cfg, K, traj = tiny["cfg"], tiny["K"], tiny["traj"]
+    gv = gpu_volume(nat, tiny)
+    n, k_max = cfg["n_particles"], 6
+    flags = nat.RF_NORMALIZE | nat.RF_COMPENSATED
+    pst = nat.pst_create(n, seed=1)
+    tr = nat.Tracker(gv, pst, nat.make_params(k_max=20, stride=cfg["stride"], flags=flags), cfg["width"],
+                     cfg["height"])
+    prev = pose_f32(traj[0])
+    # centre half way to the next pose (a proposal), axis lengths held by the caller
+    c0 = pose_f32(oracle.compose_offset(prev, 0.5 * mlp.offset(prev, traj[1])))
+    r0 = np.array([0.02, 0.02, 0.02, 0.05, 0.05, 0.05], np.float32)
+    d1, d0 = (torch.from_numpy(tiny["depths"][i]).cuda() for i in (1, 0))
+    t_prev = torch.from_numpy(prev.astype(np.float32)).cuda()
+    t_c0 = torch.from_numpy(c0.astype(np.float32)).cuda()
+    t_r = torch.from_numpy(r0).cuda()
+    out = torch.zeros(7, dtype=torch.float32, device="cuda")
+    st = nat.new_stats_buffer()
+    nat.pfo_track_frame_ex_async(tr, d1, d0, K, t_prev, out, st, init_pose_dev=t_c0, scale_dev=t_r, k_max=k_max)
+    gst = nat.stats_dict(nat.stats_from_device(st))
+    assert gst["status"] == 0 and 1 <= gst["iters"] <= k_max
+    pts = oracle.unproject(tiny["depths"][1], K, cfg["stride"])
+    res = tiny["ov"].pfo_frame(pts, tiny["depths"][0], K, prev, c0, r0.astype(np.float64), oracle.pst_uniform(n, 1),
+                               oracle_params(oracle, k_max, flags))
+    assert res["status"] == 0
+    strict = compare_traces(gst, res["trace"])
+    assert strict >= 1
+    if strict == len(res["trace"]) == gst["iters"]:
+        got = out.cpu().numpy().astype(np.float64)
+        if np.dot(got[:4], res["pose"][:4]) < 0:
+            got[:4] = -got[:4]
+        np.testing.assert_allclose(got, res["pose"], atol=2e-4)
+        np.testing.assert_allclose(t_r.cpu().numpy(), res["r1"], rtol=2e-3, atol=2e-6)
+    # the tracker's own r_0 buffer was not touched
+    np.testing.assert_allclose(tr.get_scale(), np.ones(6))
+
+
+def test_run_flag_skips_the_frame(nat, tiny):
+    import torch
+
+    cfg, K, traj = tiny["cfg"], tiny["K"], tiny["traj"]
+    gv = gpu_volume(nat, tiny)
+    pst = nat.pst_create(cfg["n_particles"], seed=1)
+    tr = nat.Tracker(gv, pst, nat.make_params(k_max=10, stride=cfg["stride"]), cfg["width"], cfg["height"])
+    d1, d0 = (torch.from_numpy(tiny["depths"][i]).cuda() for i in (1, 0))
+    prev = torch.from_numpy(pose_f32(traj[0]).astype(np.float32)).cuda()
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = torch.full((7,), 7.0, dtype=torch.float32, device="cuda")
+    r = torch.full((6,), 0.05, dtype=torch.float32, device="cuda")
+    st = nat.new_stats_buffer()
+    nat.pfo_track_frame_ex_async(tr, d1, d0, K, prev, out, st, scale_dev=r, run_flag_dev=flag)
+    torch.cuda.synchronize()
+    assert np.all(out.cpu().numpy() == 7.0) and np.all(r.cpu().numpy() == np.float32(0.05))
+    assert nat.stats_dict(nat.stats_from_device(st))["iters"] == 0
+    # flag set: the same call runs, with the iteration cap
+    flag.fill_(1)
+    nat.pfo_track_frame_ex_async(tr, d1, d0, K, prev, out, st, scale_dev=r, run_flag_dev=flag, k_max=3)
+    gst = nat.stats_dict(nat.stats_from_device(st))
+    assert gst["status"] == 0 and 1 <= gst["iters"] <= 3
+    assert np.all(np.isfinite(out.cpu().numpy())) and not np.all(out.cpu().numpy() == 7.0)
+
+
+def zero_network_params(s_value):
+    """A network whose output is mu = 0 and log scale s_value on every axis."""
+    theta = np.zeros(mlp.n_params(), np.float32)
+    b4 = mlp.unflatten(theta)[7]
+    b4[6:12] = s_value
+    return theta
+
+
+def test_learned_step_with_a_constant_proposal(oracle, nat, tiny):
+    import torch
+
+    cfg, K, traj = tiny["cfg"], tiny["K"], tiny["traj"]
+    gv = gpu_volume(nat, tiny)
+    n, k_l = cfg["n_particles"], 4
+    pst = nat.pst_create(n, seed=1)
+    tr = nat.Tracker(gv, pst, nat.make_params(k_max=20, stride=cfg["stride"]), cfg["width"], cfg["height"])
+    net = nat.MLP(16)
+    s_val = np.log(0.3)
+    net.set_params(zero_network_params(s_val))
+    params = nat.proposal_params(k_learned=k_l, theta=-1.0, kappa=2.0)
+    lp = nat.Learned(tr, gv, net, params, cfg["width"], cfg["height"])
+    prev = pose_f32(traj[0])
+    lp.start(tiny["depths"][0], K, prev)
+    sb = nat.new_learned_stats_buffer()
+    pose, status = lp.step(tiny["depths"][1], K, stats_dev=sb)
+    s = nat.learned_stats_dict(sb)
+    assert status == 0 and s["status"] == 0
+    assert s["used_fallback"] == 0 and s["chose_fallback"] == 0 and 1 <= s["iters_learned"] <= k_l
+    # the proposal: c_0 = s*_{t-1}, r_0 = kappa e^s units
+    o = np.zeros(16)
+    o[6:12] = np.float32(s_val)
+    c0, r0 = mlp.proposal(o, prev, kappa=2.0)
+    np.testing.assert_allclose(s["init_pose"], c0, atol=1e-6)
+    np.testing.assert_allclose(s["r0"], r0, rtol=2e-6)
+    # the short run is Algorithm 1 from that initialisation
+    pts = oracle.unproject(tiny["depths"][1], K, cfg["stride"])
+    res = tiny["ov"].pfo_frame(pts, tiny["depths"][0], K, prev, c0, r0.astype(np.float32).astype(np.float64),
+                               oracle.pst_uniform(n, 1), oracle_params(oracle, k_l))
+    assert res["iters"] == s["iters_learned"]
+    if abs(res["trace"][-1][4] - s["rho_learned"]) <= 1e-4 * res["trace"][-1][4]:
+        got = np.array(pose)
+        if np.dot(got[:4], res["pose"][:4]) < 0:
+            got[:4] = -got[:4]
+        np.testing.assert_allclose(got, res["pose"], atol=2e-4)
+
+
+def test_fallback_rule_and_graph_replay(nat, tiny):
+    import torch
+
+    cfg, K, traj = tiny["cfg"], tiny["K"], tiny["traj"]
+    runs = {}
+    for use_graph in (False, True):
+        gv = gpu_volume(nat, tiny)
+        pst = nat.pst_create(cfg["n_particles"], seed=1)
+        tr = nat.Tracker(gv, pst, nat.make_params(k_max=20, stride=cfg["stride"]), cfg["width"], cfg["height"])
+        tr.set_scale([0.05] * 6)
+        net = nat.MLP(16)
+        net.set_params(zero_network_params(np.log(0.2)))
+        # theta = 2: every frame after the first (rho_prev > 0) runs the fallback
+        lp = nat.Learned(tr, gv, net, nat.proposal_params(k_learned=2, theta=2.0), cfg["width"], cfg["height"])
+        lp.start(tiny["depths"][0], K, pose_f32(traj[0]))
+        sb = nat.new_learned_stats_buffer()
+        poses, stats = [], []
+        for f in range(1, 5):
+            pose, status = lp.step(tiny["depths"][f], K, use_graph=use_graph, stats_dev=sb)
+            assert status == 0
+            poses.append(pose)
+            stats.append(nat.learned_stats_dict(sb))
+        runs[use_graph] = (np.array(poses), stats)
+    poses, stats = runs[False]
+    assert stats[0]["used_fallback"] == 0  # no previous fitness yet
+    for s in stats[1:]:
+        assert s["used_fallback"] == 1 and s["iters_fallback"] >= 1
+        assert s["rho_prev"] > 0
+        assert s["chose_fallback"] == int(s["rho_fallback"] > s["rho_learned"])
+        assert s["lookups"] > 0
+    # graph replay gives the same frames bit for bit
+    np.testing.assert_array_equal(runs[True][0], poses)
+    assert [s["chose_fallback"] for s in runs[True][1]] == [s["chose_fallback"] for s in stats]

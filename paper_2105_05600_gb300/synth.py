@@ -38,6 +38,12 @@ CONFIGS = {
     "multires": dict(dims=512, voxel=0.01, trunc=0.06, dtype="i16", width=640, height=480, stride=4,
                      n_particles=10240, levels=([1024, 3072, 10240], [3, 4, 6]), k_max=20, frames=300,
                      speed=3.0, ang_speed=3.0, noise=True, wall_inset=0.20, seed=0),
+    # learned proposal: plain PFO at 10k particles labels the frames; the proposal
+    # then runs k_learned iterations (seeds 100.. train, 1000.. held out)
+    "learned": dict(dims=512, voxel=0.01, trunc=0.06, dtype="i16", width=640, height=480, stride=4,
+                    n_particles=10000, k_max=20, k_learned=5, frames=1000, speed=4.0, ang_speed=3.0, noise=True,
+                    wall_inset=0.20, seed=0, train_seeds=list(range(100, 132)), test_seeds=list(range(1000, 1004)),
+                    r_first=[0.05, 0.05, 0.05, 0.15, 0.15, 0.15], label_substeps=2),
 }
 
 
@@ -204,13 +210,75 @@ def render_depth(scene: Scene, pose, K: dict, noise_rng=None, noise_scale: float
     return z.astype(np.float32)
 
 
+def _quat_to_rot_torch(q):
+    w, x, y, z = q.unbind(-1)
+    return torch_stack3x3(
+        1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+        2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+        2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y))
+
+
+def torch_stack3x3(*e):
+    import torch
+
+    return torch.stack([torch.stack(e[0:3], -1), torch.stack(e[3:6], -1), torch.stack(e[6:9], -1)], -2)
+
+
+def render_depth_batch(scene: Scene, poses, K: dict, seed: int, noise: bool = True, noise_scale: float = 0.001,
+                       device="cuda", chunk: int = 32):
+    """Depth images (F, H, W) float32 on the device for camera->world poses (F, 7):
+    the closed-form ray casting of render_depth evaluated with torch in float64
+    on the device, for large synthetic sets.  The noise N(0, (noise_scale z^2)^2)
+    comes from a torch generator seeded with `seed`: the same distribution as
+    render_depth, not the same draws."""
+    import torch
+
+    P = torch.as_tensor(np.asarray(poses, np.float64), device=device)
+    n_f = P.shape[0]
+    W, H = int(K["width"]), int(K["height"])
+    vv, uu = torch.meshgrid(torch.arange(H, dtype=torch.float64, device=device),
+                            torch.arange(W, dtype=torch.float64, device=device), indexing="ij")
+    dc = torch.stack([(uu - K["cx"]) / K["fx"], (vv - K["cy"]) / K["fy"], torch.ones_like(uu)], -1)
+    lo = torch.as_tensor(scene.lo, dtype=torch.float64, device=device)
+    hi = torch.as_tensor(scene.hi, dtype=torch.float64, device=device)
+    inf = torch.tensor(float("inf"), dtype=torch.float64, device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    out = torch.empty((n_f, H, W), dtype=torch.float32, device=device)
+    for s in range(0, n_f, chunk):
+        p = P[s:s + chunk]
+        n = p.shape[0]
+        R = _quat_to_rot_torch(p[:, :4])
+        d = torch.einsum("hwk,njk->nhwj", dc, R)  # world ray directions, unit depth along the optical axis
+        o = p[:, 4:].view(n, 1, 1, 3)
+        tw = torch.where(d > 0, (hi - o) / d, torch.where(d < 0, (lo - o) / d, inf))
+        t = tw.amin(-1)
+        for c, r in zip(scene.centres, scene.radii):
+            oc = o - torch.as_tensor(c, dtype=torch.float64, device=device)
+            a = (d * d).sum(-1)
+            b = 2.0 * (d * oc).sum(-1)
+            cc = (oc * oc).sum(-1) - float(r) * float(r)
+            disc = b * b - 4 * a * cc
+            sq = torch.sqrt(torch.clamp(disc, min=0.0))
+            t1 = (-b - sq) / (2 * a)
+            t2 = (-b + sq) / (2 * a)
+            ts = torch.where(t1 > 1e-9, t1, torch.where(t2 > 1e-9, t2, inf))
+            t = torch.where(disc >= 0, torch.minimum(t, ts), t)
+        if noise:
+            t = t + torch.randn(t.shape, generator=gen, dtype=torch.float64, device=device) * noise_scale * t * t
+        valid = (t > K["z_min"]) & (t <= K["z_max"]) & torch.isfinite(t)
+        out[s:s + n] = torch.where(valid, t, torch.zeros_like(t)).to(torch.float32)
+    return out
+
+
 # --------------------------------------------------------------------------- trajectories
 def make_trajectory(scene: Scene, n_frames: int, speed: float, ang_speed: float, seed: int,
-                    fps: float = 30.0) -> np.ndarray:
+                    fps: float = 30.0, walk_sigma: float = 0.05) -> np.ndarray:
     """(n_frames, 7) camera->world poses at constant linear speed (m/s) and
     angular speed (rad/s); the direction and the rotation axis follow smooth
-    seeded random walks; the path reflects off planes `margin` inside the
-    walls (camera_margin) and off spheres."""
+    seeded random walks (walk_sigma per frame); the path reflects off planes
+    `margin` inside the walls (camera_margin) and off spheres.  Rendering the
+    same motion statistics at k x fps takes walk_sigma / sqrt(k)."""
     rng = np.random.default_rng(20_000 + seed)
     margin = camera_margin(scene)
     lo, hi = scene.lo + margin, scene.hi - margin
@@ -234,7 +302,7 @@ def make_trajectory(scene: Scene, n_frames: int, speed: float, ang_speed: float,
     for f in range(n_frames):
         out[f, :4] = q
         out[f, 4:] = p
-        d = d + rng.normal(size=3) * 0.05
+        d = d + rng.normal(size=3) * walk_sigma
         d /= np.linalg.norm(d)
         nxt = p + speed * dt * d
         for a in range(3):
@@ -247,7 +315,7 @@ def make_trajectory(scene: Scene, n_frames: int, speed: float, ang_speed: float,
                 n /= dist
                 d = d - 2 * (d @ n) * n
         p = np.clip(p + speed * dt * d, lo, hi)
-        axis = axis + rng.normal(size=3) * 0.05
+        axis = axis + rng.normal(size=3) * walk_sigma
         axis /= np.linalg.norm(axis)
         q = _qcanon(_qmul(axis_angle_quat(axis, ang_speed * dt), q))
     return out
@@ -269,6 +337,32 @@ def analytic_tsdf(sdf_fn, dims, voxel: float, origin, trunc: float, observed_ban
         if observed_band is not None:
             f = np.where(s < -observed_band, np.nan, f)
         F[k] = f
+    return F
+
+
+def analytic_tsdf_torch(scene: Scene, dims, voxel: float, origin, trunc: float, observed_band: float | None = None,
+                        device="cuda"):
+    """analytic_tsdf evaluated with torch on the device (float32 values, NaN where
+    unobserved), for 512^3 volumes; shaped (dz, dy, dx)."""
+    import torch
+
+    dx, dy, dz = dims
+    o = [float(v) for v in origin]
+    lo = torch.as_tensor(scene.lo, dtype=torch.float64, device=device)
+    hi = torch.as_tensor(scene.hi, dtype=torch.float64, device=device)
+    yy, xx = torch.meshgrid((torch.arange(dy, dtype=torch.float64, device=device) + 0.5) * voxel + o[1],
+                            (torch.arange(dx, dtype=torch.float64, device=device) + 0.5) * voxel + o[0], indexing="ij")
+    F = torch.empty((dz, dy, dx), dtype=torch.float32, device=device)
+    for k in range(dz):
+        p = torch.stack([xx, yy, torch.full_like(xx, (k + 0.5) * voxel + o[2])], -1)
+        d = torch.minimum(p - lo, hi - p).amin(-1)
+        for c, r in zip(scene.centres, scene.radii):
+            d = torch.minimum(d, torch.linalg.norm(p - torch.as_tensor(c, dtype=torch.float64, device=device), dim=-1)
+                              - float(r))
+        f = torch.clamp(d / trunc, -1.0, 1.0)
+        if observed_band is not None:
+            f = torch.where(d < -observed_band, torch.full_like(f, float("nan")), f)
+        F[k] = f.to(torch.float32)
     return F
 
 

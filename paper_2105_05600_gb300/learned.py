@@ -172,70 +172,103 @@ def validation_loss(net, X, Y, va_idx, batch: int) -> float:
 
 
 # ----------------------------------------------------------------------------- evaluation
-def run_plain(nat, spec, traj, K, depths, k_max=None):
-    """Plain PFO over a sequence (rf_sequence_step). Returns (poses, seconds of the
-    tracked frames measured with CUDA events, lookups)."""
+class _FrameTimer:
+    """CUDA events around each timed frame (frames >= `warmup`); with `flush`
+    (a device buffer larger than L2) the buffer is rewritten before each timed
+    frame, outside the events."""
+
+    def __init__(self, n, warmup=0, flush=None):
+        import torch
+
+        self.ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        self.warmup, self.flush = warmup, flush
+
+    def begin(self, f):
+        if f > self.warmup:
+            if self.flush is not None:
+                self.flush.fill_(f & 0xFF)
+            self.ev[f][0].record()
+
+    def end(self, f):
+        if f > self.warmup:
+            self.ev[f][1].record()
+
+    def seconds(self, n):
+        return sum(self.ev[f][0].elapsed_time(self.ev[f][1]) for f in range(self.warmup + 1, n)) / 1e3
+
+
+def run_plain(nat, spec, traj, K, depths, k_max=None, warmup=0, flush=None):
+    """Plain PFO over a sequence (rf_sequence_step).  Returns (poses, seconds of the
+    frames after `warmup` measured with CUDA events, their lookups)."""
     import torch
 
     vol, pst, tr = _tracker(nat, spec, k_max)
     nat.rf_sequence_start(tr, depths[0], K, traj[0])
-    out = torch.zeros((len(depths), 7), dtype=torch.float32, device="cuda")
+    n = len(depths)
+    out = torch.zeros((n, 7), dtype=torch.float32, device="cuda")
     pose_buf = torch.zeros(7, dtype=torch.float32, device="cuda")
     stats = nat.new_stats_buffer()
-    lookups = torch.zeros(len(depths), dtype=torch.int64, device="cuda")
+    lookups = torch.zeros(n, dtype=torch.int64, device="cuda")
     out[0] = torch.as_tensor(traj[0], dtype=torch.float32)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tm = _FrameTimer(n, warmup, flush)
     torch.cuda.synchronize()
-    e0.record()
-    for f in range(1, len(depths)):
+    for f in range(1, n):
+        tm.begin(f)
         nat.rf_sequence_step(tr, depths[f], K, want_host_pose=False, out_pose_dev=pose_buf, stats_dev=stats)
+        tm.end(f)
         out[f].copy_(pose_buf)
         lookups[f] = stats[16:24].view(torch.int64)[0]  # rf_frame_stats.lookups
-    e1.record()
     torch.cuda.synchronize()
-    return out.cpu().numpy().astype(np.float64), e0.elapsed_time(e1) / 1e3, int(lookups.sum().item())
+    return out.cpu().numpy().astype(np.float64), tm.seconds(n), int(lookups[warmup + 1:].sum().item())
 
 
-def run_learned(nat, spec, traj, K, depths, net, params, use_graph=True):
-    """Proposal-driven tracking over a sequence (rf_learned_step).  Returns (poses,
-    seconds, lookups, fallback count, mean learned iterations)."""
+def run_learned(nat, spec, traj, K, depths, net, params, use_graph=True, warmup=0, flush=None):
+    """Proposal-driven tracking over a sequence (rf_learned_step).  Returns dict(poses,
+    seconds and lookups of the frames after `warmup`, fallback runs / kept, mean
+    learned iterations, frames with a non-zero status)."""
     import torch
 
     vol, pst, tr = _tracker(nat, spec)
     lp = nat.Learned(tr, vol, net, params, spec["width"], spec["height"])
     lp.start(depths[0], K, traj[0])
-    out = torch.zeros((len(depths), 7), dtype=torch.float32, device="cuda")
+    n = len(depths)
+    out = torch.zeros((n, 7), dtype=torch.float32, device="cuda")
     out[0] = torch.as_tensor(traj[0], dtype=torch.float32)
     pose_buf = torch.zeros(7, dtype=torch.float32, device="cuda")
     sb = nat.new_learned_stats_buffer()
-    rec = torch.zeros((len(depths), sb.numel()), dtype=torch.uint8, device="cuda")
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rec = torch.zeros((n, sb.numel()), dtype=torch.uint8, device="cuda")
+    tm = _FrameTimer(n, warmup, flush)
     torch.cuda.synchronize()
-    e0.record()
-    for f in range(1, len(depths)):
+    for f in range(1, n):
+        tm.begin(f)
         lp.step(depths[f], K, use_graph=use_graph, want_host_pose=False, out_pose_dev=pose_buf, stats_dev=sb)
+        tm.end(f)
         out[f].copy_(pose_buf)
         rec[f].copy_(sb)
-    e1.record()
     torch.cuda.synchronize()
-    st = [nat.learned_stats_dict(rec[f]) for f in range(1, len(depths))]
-    return (out.cpu().numpy().astype(np.float64), e0.elapsed_time(e1) / 1e3, sum(s["lookups"] for s in st),
-            sum(s["used_fallback"] for s in st), float(np.mean([s["iters_learned"] for s in st])),
-            sum(s["chose_fallback"] for s in st), sum(1 for s in st if s["status"] != 0))
+    st = [nat.learned_stats_dict(rec[f]) for f in range(1, n)]
+    timed = st[warmup:]
+    return dict(poses=out.cpu().numpy().astype(np.float64), seconds=tm.seconds(n),
+                lookups=sum(s["lookups"] for s in timed), fallbacks=sum(s["used_fallback"] for s in st),
+                fallback_kept=sum(s["chose_fallback"] for s in st),
+                iters=float(np.mean([s["iters_learned"] for s in st])),
+                failed=sum(1 for s in st if s["status"] != 0))
 
 
-def evaluate(nat, spec, seeds, n_frames, net, params, use_graph=True):
+def evaluate(nat, spec, seeds, n_frames, net, params, use_graph=True, warmup=0, flush=None):
     """A/B on held-out sequences: plain PFO (spec k_max) against the learned
-    proposal + k_learned iterations.  Per sequence: frames/s, ATE, lookups."""
+    proposal + k_learned iterations, same frames.  Per sequence: frames/s of the
+    frames after `warmup`, ATE over all tracked frames, lookups, fallbacks."""
     rows = []
     for s in seeds:
         _, traj, K, depths = make_sequence(spec, s, n_frames)
-        pp, tp, lkp = run_plain(nat, spec, traj, K, depths)
-        pl, tl, lkl, fb, it, chose, bad = run_learned(nat, spec, traj, K, depths, net, params, use_graph)
+        pp, tp, lkp = run_plain(nat, spec, traj, K, depths, warmup=warmup, flush=flush)
+        rl = run_learned(nat, spec, traj, K, depths, net, params, use_graph, warmup=warmup, flush=flush)
         ap, _ = metrics.ate(pp, traj)
-        al, _ = metrics.ate(pl, traj)
-        nf = n_frames - 1
-        rows.append(dict(seed=s, plain_fps=nf / tp, learned_fps=nf / tl, plain_ate_cm=100 * ap,
-                         learned_ate_cm=100 * al, plain_lookups=lkp, learned_lookups=lkl, fallbacks=fb,
-                         fallback_kept=chose, learned_iters=it, failed_frames=bad))
+        al, _ = metrics.ate(rl["poses"], traj)
+        nf = n_frames - 1 - warmup
+        rows.append(dict(seed=s, frames=nf, plain_s=tp, learned_s=rl["seconds"], plain_fps=nf / tp,
+                         learned_fps=nf / rl["seconds"], plain_ate_cm=100 * ap, learned_ate_cm=100 * al,
+                         plain_lookups=lkp, learned_lookups=rl["lookups"], fallbacks=rl["fallbacks"],
+                         fallback_kept=rl["fallback_kept"], learned_iters=rl["iters"], failed_frames=rl["failed"]))
     return rows

@@ -678,6 +678,78 @@ def run_learned_bench(args):
     return res
 
 
+# ----------------------------------------------------------------------------- network microbenchmark
+def run_mlp_bench(args):
+    """The proposal network alone: Adam training steps (batch 1024) and forward
+    passes (batch 4096 and 1) on synthetic features, timed with CUDA events; the
+    tensor-core roofline of the training step (2 x 348160 FLOPs per sample forward,
+    3x that per trained sample) against the measured bf16 GEMM peak."""
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2105_05600_gb300 import build, learned
+
+    build.build()
+    from paper_2105_05600_gb300 import _native as nat
+
+    rng = np.random.default_rng(7 + rank)
+    n_all, B, BF = 8192, 1024, 4096
+    X = np.zeros((n_all, 832), np.float32)
+    X[:, :774] = np.clip(rng.normal(size=(n_all, 774)), -8, 8)
+    Xg = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    Yg = torch.from_numpy(rng.normal(size=(n_all, 6)).astype(np.float32)).cuda()
+    net = nat.MLP(BF)
+    net.set_params(learned.init_params(0))
+    idx = [torch.as_tensor(rng.choice(n_all, B, replace=False).astype(np.int32), device="cuda")
+           for _ in range(args.warmup + args.steps)]
+    out = torch.empty((BF, 16), dtype=torch.float32, device="cuda")
+    for i in range(args.warmup):
+        net.train_step(Xg, Yg, B, 1e-4, idx=idx[i])
+        net.forward(Xg[:BF], out=out)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3 * args.steps)]
+    for k in range(args.steps):
+        a, b = ev[k]
+        a.record()
+        net.train_step(Xg, Yg, B, 1e-4, idx=idx[args.warmup + k])
+        b.record()
+    for k in range(args.steps):
+        a, b = ev[args.steps + k]
+        a.record()
+        net.forward(Xg[:BF], out=out)
+        b.record()
+    for k in range(args.steps):
+        a, b = ev[2 * args.steps + k]
+        a.record()
+        net.forward(Xg[:1], out=out[:1])
+        b.record()
+    torch.cuda.synchronize()
+    assert net.status() == 0
+    t = [statistics.median(a.elapsed_time(b) for a, b in ev[i * args.steps:(i + 1) * args.steps]) / 1e3
+         for i in range(3)]
+    fl = 2 * sum(o * i for o, i in learned.LAYERS)
+    peak = 1873.7
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peak = float(json.load(open(pk))["bf16_tflops"])
+    train_tf = 3 * fl * B / t[0] / 1e12
+    return {
+        "metric": "proposal network training samples/s (own tcgen05 GEMM kernels)", "value": B / t[0],
+        "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t[0],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 x bf16 -> f32",
+        "data": "synthetic features", "config": {"workload": "MLP 832-256-256-256-16, Adam step at batch 1024 "
+                                                              "(gather, forward, loss, backward, update)",
+                                                  "l2": "not flushed: the whole working set (< 20 MB) is L2-resident by design"},
+        "forward_b4096_ms": 1e3 * t[1], "forward_b1_ms": 1e3 * t[2],
+        "forward_b4096_tflops": fl * BF / t[1] / 1e12,
+        "roofline": {"bound": "tensor", "achieved": train_tf, "peak": peak, "unit": "TFLOP/s",
+                     "frac": train_tf / peak, "traffic": None, "kernel": "umma_gemm_kernel (training step: 11 GEMMs)",
+                     "note": "measured bf16 burst peak; products of 256-wide layers are launch- and latency-bound"},
+        "gpu_launches": args.steps * (18 + 8),  # train step: gather, 11 GEMMs, loss, 4 bias, Adam; 2 x 4 forward GEMMs
+    }
+
+
 def metrics_ate(est, gt):
     from paper_2105_05600_gb300 import metrics
 
@@ -688,6 +760,10 @@ def main():
     args = parse()
     from paper_2105_05600_gb300 import synth
 
+    if args.config == "mlp":
+        print(json.dumps(run_mlp_bench(args) if args.impl != "reference" else {
+            "impl": "reference", "unavailable": "mlp config: no reference network timing; see --config paper"}))
+        return
     if args.config == "learned":
         res = run_learned_bench(args) if args.impl != "reference" else {
             "impl": "reference", "unavailable": "learned config: the oracle has no end-to-end tracker timing; the "

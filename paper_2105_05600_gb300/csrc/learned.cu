@@ -47,44 +47,63 @@ __device__ void pose_offset(const float *a, const float *b, double d[6])
     }
 }
 
-// One CTA of N_RES threads, thread (i, j) = cell (i, j): mean valid depth of the
-// cell in both frames (FP64 sums), the clipped residual, then the offset
-// features and the zero padding.
-__global__ void features_kernel(const float *depth, const float *prev_depth, Intr K, const float *pose_prev2,
-                                const float *pose_prev, bf16 *x)
+constexpr int FEAT_WARPS = 8;                             // cells per CTA (one warp each)
+constexpr int FEAT_CTAS = N_RES / FEAT_WARPS + 1;          // + one CTA for the offset / padding entries
+
+// One warp per grid cell (i, j): the lanes stride over the cell's pixels, sum
+// the valid depths of both frames in FP64 and reduce in a fixed shuffle order;
+// lane 0 writes the clipped residual.  The last CTA writes the offset features
+// and the zero padding.  (FP64 is spread over the grid: GB300's per-SM FP64
+// rate is low, one CTA of FP64 sums would serialise on one SM.)
+__global__ void __launch_bounds__(FEAT_WARPS * 32) features_kernel(const float *depth, const float *prev_depth,
+                                                                   Intr K, const float *pose_prev2,
+                                                                   const float *pose_prev, bf16 *x)
 {
-    const int t = threadIdx.x;
-    if (t < N_RES) {
-        const int i = t % GRID_W, j = t / GRID_W;
-        const int c0 = (i * K.width) / GRID_W, c1 = ((i + 1) * K.width) / GRID_W;
-        const int r0 = (j * K.height) / GRID_H, r1 = ((j + 1) * K.height) / GRID_H;
-        double sc = 0.0, sp = 0.0;
-        int nc = 0, np = 0;
-        for (int r = r0; r < r1; ++r)
-            for (int c = c0; c < c1; ++c) {
-                const size_t o = (size_t)r * K.width + c;
-                const float zc = __ldg(&depth[o]), zp = __ldg(&prev_depth[o]);
-                if (zc > K.z_min && zc <= K.z_max) {
-                    sc += zc;
-                    ++nc;
-                }
-                if (zp > K.z_min && zp <= K.z_max) {
-                    sp += zp;
-                    ++np;
-                }
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == FEAT_CTAS - 1) {
+        const int t = N_RES + threadIdx.x;
+        if (t < RF_MLP_IN) {
+            double v = 0.0;
+            if (t < RF_MLP_IN_USED) {
+                double d[6];
+                pose_offset(pose_prev2, pose_prev, d);
+                v = d[t - N_RES] / c_units[t - N_RES];
             }
+            x[t] = __double2bfloat16(v);
+        }
+        return;
+    }
+    const int cell = blockIdx.x * FEAT_WARPS + (threadIdx.x >> 5);
+    const int i = cell % GRID_W, j = cell / GRID_W;
+    const int c0 = (i * K.width) / GRID_W, c1 = ((i + 1) * K.width) / GRID_W;
+    const int r0 = (j * K.height) / GRID_H, r1 = ((j + 1) * K.height) / GRID_H;
+    const int cw = c1 - c0, npix = cw * (r1 - r0);
+    double sc = 0.0, sp = 0.0;
+    int nc = 0, np = 0;
+    for (int p = lane; p < npix; p += 32) {
+        const int r = r0 + p / cw, c = c0 + p % cw;
+        const size_t o = (size_t)r * K.width + c;
+        const float zc = __ldg(&depth[o]), zp = __ldg(&prev_depth[o]);
+        if (zc > K.z_min && zc <= K.z_max) {
+            sc += zc;
+            ++nc;
+        }
+        if (zp > K.z_min && zp <= K.z_max) {
+            sp += zp;
+            ++np;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        sp += __shfl_xor_sync(0xffffffffu, sp, o);
+        nc += __shfl_xor_sync(0xffffffffu, nc, o);
+        np += __shfl_xor_sync(0xffffffffu, np, o);
+    }
+    if (lane == 0) {
         double f = 0.0;
         if (nc > 0 && np > 0)
             f = fmin(fmax((sc / nc - sp / np) / S_Z, -RES_CLIP), RES_CLIP);
-        x[t] = __double2bfloat16(f);
-    } else if (t < RF_MLP_IN) {
-        double v = 0.0;
-        if (t < RF_MLP_IN_USED) {
-            double d[6];
-            pose_offset(pose_prev2, pose_prev, d);
-            v = d[t - N_RES] / c_units[t - N_RES];
-        }
-        x[t] = __double2bfloat16(v);
+        x[cell] = __double2bfloat16(f);
     }
 }
 
@@ -259,8 +278,8 @@ static rf_status learned_enqueue(rf_learned lp, const rf_intrinsics *K, rf_learn
                                  cudaStream_t s)
 {
     LearnedState *S = lp->S;
-    features_kernel<<<1, RF_MLP_IN, 0, s>>>(lp->depth_cur, lp->depth_prev, to_intr(*K), S->hist[0], S->hist[1],
-                                            reinterpret_cast<bf16 *>(lp->x));
+    features_kernel<<<FEAT_CTAS, FEAT_WARPS * 32, 0, s>>>(lp->depth_cur, lp->depth_prev, to_intr(*K), S->hist[0],
+                                                          S->hist[1], reinterpret_cast<bf16 *>(lp->x));
     RF_CUDA(cudaGetLastError());
     rf_status st = rf_mlp_forward(lp->net, lp->x, 1, lp->out, s);
     if (st != RF_OK)
@@ -315,8 +334,8 @@ rf_status rf_proposal_features(const float *depth_dev, const float *prev_depth_d
 {
     RF_CHECK_ARG(depth_dev && prev_depth_dev && K && pose_prev2_dev && pose_prev_dev && x_dev, "null pointer");
     RF_CHECK_ARG(K->width >= 1 && K->height >= 1, "bad frame size");
-    features_kernel<<<1, RF_MLP_IN, 0, (cudaStream_t)stream>>>(depth_dev, prev_depth_dev, to_intr(*K), pose_prev2_dev,
-                                                               pose_prev_dev, reinterpret_cast<bf16 *>(x_dev));
+    features_kernel<<<FEAT_CTAS, FEAT_WARPS * 32, 0, (cudaStream_t)stream>>>(
+        depth_dev, prev_depth_dev, to_intr(*K), pose_prev2_dev, pose_prev_dev, reinterpret_cast<bf16 *>(x_dev));
     RF_CUDA(cudaGetLastError());
     return RF_OK;
 }

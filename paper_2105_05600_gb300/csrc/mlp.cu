@@ -404,28 +404,32 @@ __global__ void gather_kernel(const bf16 *x_all, const float *y_all, const int *
 
 // Loss (mean over the batch of sum_d 1/2 r^2 (1 + e^{-2s}) + s, r = y - mu,
 // s = clamp(o_s, -6, 6)) and its gradient with respect to the 16 outputs,
-// computed in FP64 and stored as bfloat16 (row-major and transposed) for the
-// backward products.  One CTA, one thread per sample (B <= 1024).
+// computed in FP32 per sample and stored as bfloat16 (row-major and
+// transposed) for the backward products; the batch sum runs in FP64 in a fixed
+// order.  One CTA, one thread per sample (B <= 1024).
 __global__ void loss_kernel(const float *out, const float *y, int B, bf16 *g, bf16 *gt, float *loss)
 {
     __shared__ double red[32];
     const int b = threadIdx.x;
     double l = 0.0;
     if (b < B) {
-        double gr[RF_MLP_OUT];
+        float gr[RF_MLP_OUT];
         for (int j = 0; j < RF_MLP_OUT; ++j)
-            gr[j] = 0.0;
+            gr[j] = 0.f;
+        const float inv_b = 1.f / (float)B;
+        float lf = 0.f;
         for (int d = 0; d < 6; ++d) {
-            const double mu = out[b * RF_MLP_OUT + d], sr = out[b * RF_MLP_OUT + 6 + d];
-            const double s = fmin(fmax(sr, -6.0), 6.0);
-            const double r = (double)y[b * 6 + d] - mu;
-            const double ex = exp(-2.0 * s);
-            l += 0.5 * r * r * (1.0 + ex) + s;
-            gr[d] = -r * (1.0 + ex) / B;
-            gr[6 + d] = (sr > -6.0 && sr < 6.0) ? (1.0 - r * r * ex) / B : 0.0;
+            const float mu = out[b * RF_MLP_OUT + d], sr = out[b * RF_MLP_OUT + 6 + d];
+            const float s = fminf(fmaxf(sr, -6.f), 6.f);
+            const float r = y[b * 6 + d] - mu;
+            const float ex = expf(-2.f * s);
+            lf += 0.5f * r * r * (1.f + ex) + s;
+            gr[d] = -r * (1.f + ex) * inv_b;
+            gr[6 + d] = (sr > -6.f && sr < 6.f) ? (1.f - r * r * ex) * inv_b : 0.f;
         }
+        l = lf;
         for (int j = 0; j < RF_MLP_OUT; ++j) {
-            const bf16 h = __double2bfloat16(gr[j]);
+            const bf16 h = __float2bfloat16_rn(gr[j]);
             g[b * RF_MLP_OUT + j] = h;
             gt[(size_t)j * B + b] = h;
         }

@@ -750,6 +750,60 @@ def run_mlp_bench(args):
     }
 
 
+# ----------------------------------------------------------------------------- ablation flags
+ABLATIONS = [("full", 0), ("no_overlap", -1), ("no_normalize", -2), ("no_kahan", -4), ("nearest", 8),
+             ("rho_ref_centre", 16), ("se3_product", 64)]
+
+
+def run_ablation_bench(args):
+    """Plain PFO with each ablation flag (Sec. 5, Table ablt-tsdf and the PST
+    rescaling study) on the same held-out sequences: ATE, frame-to-frame error,
+    iterations and frames/s per variant.  value = frames/s of the full method."""
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2105_05600_gb300 import build, learned, metrics, synth
+
+    build.build()
+    from paper_2105_05600_gb300 import _native as nat
+
+    spec = dict(synth.CONFIGS["learned"], speed=1.5, ang_speed=0.75)  # FastCaMo-Synth mean speeds
+    seeds = [s + 1000 * rank for s in spec["test_seeds"][:args.test_seqs or 3]]
+    frames = args.frames or 200
+    W = max(3, args.warmup)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    seqs = [learned.make_sequence(spec, s, frames) for s in seeds]
+    clocks = ClockSampler(local).start()
+    table = {}
+    for name, f in ABLATIONS:
+        flags = nat.RF_DEFAULT_FLAGS & ~(-f) if f < 0 else nat.RF_DEFAULT_FLAGS | f
+        ates, rpes, secs, lks = [], [], 0.0, 0
+        for _, traj, K, depths in seqs:
+            p, t, lk = learned.run_plain(nat, spec, traj, K, depths, warmup=W, flush=flush, flags=flags)
+            ates.append(100 * metrics.ate(p, traj)[0])
+            rpes.append(100 * float(np.median(np.linalg.norm(np.diff(p[:, 4:], axis=0) - np.diff(traj[:, 4:], axis=0),
+                                                             axis=1))))
+            secs += t
+            lks += lk
+        nf = len(seqs) * (frames - 1 - W)
+        table[name] = {"flags": int(flags), "ate_cm": [round(a, 2) for a in ates], "ate_cm_mean": float(np.mean(ates)),
+                       "rpe_median_cm": [round(r, 2) for r in rpes], "frames_per_s": nf / secs,
+                       "lookups_per_frame": lks / nf}
+    clk = clocks.stop()
+    full = table["full"]
+    return {
+        "metric": METRIC, "value": full["frames_per_s"], "unit": "frames/s", "n_gpus": world,
+        "steps": len(seqs) * (frames - 1 - W), "warmup": W, "ms_per_step": 1e3 / full["frames_per_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (held-out seeds)",
+        "config": {"workload": f"ablation of plain PFO: 512^3 int16, 640x480 stride 4, 10000 particles, <= 20 "
+                               f"iterations, {spec['speed']:g} m/s + {spec['ang_speed']:g} rad/s, {len(seqs)} sequences "
+                               f"x {frames} frames", "l2": "flushed before every timed frame"},
+        "ablation": table, "gpu_launches": 3 * len(ABLATIONS) * len(seqs) * (frames - 1 - W), "clocks": clk,
+    }
+
+
 def metrics_ate(est, gt):
     from paper_2105_05600_gb300 import metrics
 
@@ -760,6 +814,10 @@ def main():
     args = parse()
     from paper_2105_05600_gb300 import synth
 
+    if args.config == "ablation":
+        print(json.dumps(run_ablation_bench(args) if args.impl != "reference" else {
+            "impl": "reference", "unavailable": "ablation config: see --config paper"}))
+        return
     if args.config == "mlp":
         print(json.dumps(run_mlp_bench(args) if args.impl != "reference" else {
             "impl": "reference", "unavailable": "mlp config: no reference network timing; see --config paper"}))

@@ -33,11 +33,12 @@ def make_sequence(spec: dict, seed: int, n_frames: int, substeps: int = 1):
     return scene, traj, K, depths
 
 
-def _tracker(nat, spec, k_max=None):
+def _tracker(nat, spec, k_max=None, flags=None):
     vol = nat.Volume(spec["dims"], spec["voxel"], spec["trunc"], (0, 0, 0), spec["dtype"])
     pst = nat.pst_create(spec["n_particles"], seed=1)
-    tr = nat.Tracker(vol, pst, nat.make_params(k_max=k_max or spec["k_max"], stride=spec["stride"]),
-                     spec["width"], spec["height"])
+    params = nat.make_params(k_max=k_max or spec["k_max"], stride=spec["stride"],
+                             flags=nat.RF_DEFAULT_FLAGS if flags is None else flags)
+    tr = nat.Tracker(vol, pst, params, spec["width"], spec["height"])
     tr.set_scale(spec.get("r_first", [1.0] * 6))  # r_0 of the first tracked frame
     return vol, pst, tr
 
@@ -197,12 +198,12 @@ class _FrameTimer:
         return sum(self.ev[f][0].elapsed_time(self.ev[f][1]) for f in range(self.warmup + 1, n)) / 1e3
 
 
-def run_plain(nat, spec, traj, K, depths, k_max=None, warmup=0, flush=None):
+def run_plain(nat, spec, traj, K, depths, k_max=None, warmup=0, flush=None, flags=None):
     """Plain PFO over a sequence (rf_sequence_step).  Returns (poses, seconds of the
     frames after `warmup` measured with CUDA events, their lookups)."""
     import torch
 
-    vol, pst, tr = _tracker(nat, spec, k_max)
+    vol, pst, tr = _tracker(nat, spec, k_max, flags)
     nat.rf_sequence_start(tr, depths[0], K, traj[0])
     n = len(depths)
     out = torch.zeros((n, 7), dtype=torch.float32, device="cuda")

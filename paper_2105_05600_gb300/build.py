@@ -37,7 +37,7 @@ def _sources():
 
 def _fingerprint() -> str:
     h = hashlib.sha256()
-    for f in _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "rosefusion.h")]:
+    for f in _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(glob.glob(os.path.join(INCLUDE, "*.h"))):
         h.update(f.encode())
         with open(f, "rb") as fh:
             h.update(fh.read())

@@ -23,10 +23,18 @@ constexpr int MIN_CHUNK = 32;         // fewest points per work unit
 constexpr int UNITS_PER_WARP = RF_UNITS_PER_WARP;  // target work units per warp and iteration
 constexpr int APW = 16;               // doubles per CTA in the APS partials
 constexpr int MAX_CTAS_PER_SM = 2048 / FIT_THREADS;  // bound for grid-sized scratch
-// CTAs of the persistent kernel resident per SM (register budget 65536 / (256 * n))
+// CTAs of the persistent kernel resident per SM (register budget 65536 / (256 * n)).
+// Measured on the paper-scale frame: groups of 6 lookups at 2 CTAs per SM 312.7 G
+// lookups/s, 8 at 2: 306.5, 4 at 3: 299.1 (more loads in flight per warp beat
+// more warps).
 #ifndef RF_PFO_MIN_BLOCKS
-#define RF_PFO_MIN_BLOCKS 3
+#define RF_PFO_MIN_BLOCKS 2
 #endif
+// lookups whose loads are issued together in the trilinear loop
+#ifndef RF_GROUP
+#define RF_GROUP 6
+#endif
+constexpr int GROUP = RF_GROUP;
 
 // ------------------------------------------------------------------ small helpers
 __device__ __forceinline__ long long global_ns()
@@ -143,25 +151,25 @@ __device__ __forceinline__ void fitness_points(const CellView &V, const float4 *
         return L1 ? fabsf(psi) : psi * psi;
     };
     if (!Mode<MODE>::nearest) {
-        // groups of 4 lookups: all class loads, then all cell loads, then the
+        // groups of GROUP lookups: all class loads, then all cell loads, then the
         // arithmetic, so each group pays the load latency once; a plain FP32
-        // partial of <= 4 terms in [0, 1] is then added with compensation
-        for (; j + 4 <= cnt; j += 4) {
-            CellRef c[4];
-            CellData<DT> d[4];
+        // partial of <= GROUP terms in [0, 1] is then added with compensation
+        for (; j + GROUP <= cnt; j += GROUP) {
+            CellRef c[GROUP];
+            CellData<DT> d[GROUP];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < GROUP; ++u) {
                 const float4 x = spts[j + u];
                 cell_locate(V, fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, t0))),
                             fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, t1))),
                             fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, t2))), c[u]);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < GROUP; ++u)
                 cell_fetch<DT>(V, c[u], d[u]);
             float grp = 0.f;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < GROUP; ++u) {
                 float psi;
                 const bool ok = cell_eval<DT>(c[u], d[u], psi);
                 grp += term(ok, psi);

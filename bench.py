@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--train-frames", type=int, default=None, help="learned config: 30 Hz frames per training sequence")
     ap.add_argument("--test-seqs", type=int, default=None, help="learned config: held-out sequences")
     ap.add_argument("--frames", type=int, default=None, help="learned config: frames per held-out sequence")
+    ap.add_argument("--speed", type=float, default=None, help="learned / ablation config: linear speed (m/s)")
+    ap.add_argument("--ang-speed", type=float, default=None, help="learned / ablation config: angular speed (rad/s)")
     return ap.parse_args()
 
 
@@ -571,6 +573,10 @@ def run_learned_bench(args):
     from paper_2105_05600_gb300 import _native as nat
 
     spec = dict(synth.CONFIGS["learned"])
+    if args.speed is not None:
+        spec["speed"] = args.speed
+    if args.ang_speed is not None:
+        spec["ang_speed"] = args.ang_speed
     n_train = args.train_seqs or len(spec["train_seeds"])
     train_frames = args.train_frames or 500
     n_test = args.test_seqs or len(spec["test_seeds"])
@@ -664,7 +670,10 @@ def run_learned_bench(args):
         "labels": {"plain_60hz_ate_cm_mean": float(np.mean(label_ate)), "samples": int(len(seq))},
         "network": {"train_step_ms": 1e3 * t_train, "forward_b1_ms": 1e3 * t_fwd,
                     "train_tflops": 3 * flops_fwd * 512 / t_train / 1e12,
-                    "val_loss": hist["val"], "train_seconds": hist["seconds"],
+                    "val_loss": [round(v, 4) for v in hist["val"]],
+                    "val_offset_err": [round(v, 4) for v in hist["val_offset_err"]],
+                    "zero_offset_err": hist["zero_offset_err"], "scale_calibration": hist["scale_calibration"],
+                    "best_epoch": hist.get("best_epoch"), "train_seconds": hist["seconds"],
                     "note": "tcgen05 GEMMs on 128x128 tiles; at these sizes every product is launch- and "
                             "latency-bound"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -768,7 +777,7 @@ def run_ablation_bench(args):
     build.build()
     from paper_2105_05600_gb300 import _native as nat
 
-    spec = dict(synth.CONFIGS["learned"], speed=1.5, ang_speed=0.75)  # FastCaMo-Synth mean speeds
+    spec = dict(synth.CONFIGS["learned"], speed=args.speed or 1.5, ang_speed=args.ang_speed or 0.75)  # FastCaMo-Synth means
     seeds = [s + 1000 * rank for s in spec["test_seeds"][:args.test_seqs or 3]]
     frames = args.frames or 200
     W = max(3, args.warmup)

@@ -34,7 +34,8 @@
  *            product; products accumulate in FP32.  Parameters: one flat float
  *            vector W1 (row-major), b1, W2, b2, W3, b3, W4, b4.  Columns 774..831
  *            of W1 and rows 12..15 of W4 / entries 12..15 of b4 are padding.
- *  output    mu = o[0..5] (offset from s*_{t-1} to s*_t over units),
+ *  output    mu = x[768..773] + o[0..5]: the offset from s*_{t-1} to s*_t over
+ *            units, as the previous offset plus the network's correction;
  *            s = clamp(o[6..11], -6, 6) (log scale per axis).
  *  loss      mean over the batch of sum_d 1/2 r_d^2 (1 + exp(-2 s_d)) + s_d,
  *            r = y - mu (squared error plus a Gaussian negative log-likelihood);
@@ -132,11 +133,13 @@ void rf_proposal_default_params(rf_proposal_params *p);
 /*
  * rf_proposal_apply -- c_0 and r_0 (definition above) from one network output.
  *   out_dev        device float[RF_MLP_OUT]
+ *   x_dev          device uint16[RF_MLP_IN]: the input row the output came from
+ *                  (its previous-offset entries are the base of mu)
  *   pose_prev_dev  device float[7], s*_{t-1}
  *   init_pose_dev  device float[7] receives c_0;  scale_dev device float[6] r_0
  */
-rf_status rf_proposal_apply(const float *out_dev, const float *pose_prev_dev, const rf_proposal_params *p,
-                            float *init_pose_dev, float *scale_dev, void *stream);
+rf_status rf_proposal_apply(const float *out_dev, const uint16_t *x_dev, const float *pose_prev_dev,
+                            const rf_proposal_params *p, float *init_pose_dev, float *scale_dev, void *stream);
 
 /* -------------------------------------------------- learned tracking --- */
 /*

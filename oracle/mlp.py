@@ -19,7 +19,8 @@ centre offset and per-axis scale that replace that initialisation.
                       exact (FP64) sums
     loss ............ per output axis 1/2 r^2 (1 + e^{-2s}) + s: squared error
                       on the mean plus a Gaussian negative log-likelihood for
-                      the log scale s (clamped to [-6, 6])
+                      the log scale s (clamped to [-6, 6]); the mean offset is
+                      the previous offset (an input) plus the first 6 outputs
     backward ........ hand-written reverse mode of the above; in pure FP64 mode
                       it is the exact gradient (checked by finite differences)
     adam ............ Kingma & Ba 2015, Algorithm 1 (bias-corrected moments)
@@ -157,12 +158,18 @@ def forward(theta, X, round_bf16=True):
     return O, acts
 
 
-def loss_and_grad_out(O, Y):
+def mean_offset(O, V):
+    """mu = V + O[:, 0:6]: the previous offset (input columns 768..773, as the
+    network sees them) plus the network's correction."""
+    return np.asarray(V, np.float64) + O[:, 0:6]
+
+
+def loss_and_grad_out(O, Y, V):
     """Mean over the batch of sum_d [1/2 r_d^2 (1 + e^{-2 s_d}) + s_d], r = y - mu,
-    mu = O[:, 0:6], s = clamp(O[:, 6:12], -6, 6); returns (L, dL/dO) with dL/dO
+    mu = V + O[:, 0:6], s = clamp(O[:, 6:12], -6, 6); returns (L, dL/dO) with dL/dO
     zero in the padding columns and where the clamp is active."""
     B = O.shape[0]
-    mu, s_raw = O[:, 0:6], O[:, 6:12]
+    mu, s_raw = mean_offset(O, V), O[:, 6:12]
     s = np.clip(s_raw, -S_CLAMP, S_CLAMP)
     r = Y - mu
     e = np.exp(-2.0 * s)
@@ -193,14 +200,19 @@ def backward(theta, acts, G, round_bf16=True):
     return grad
 
 
+def velocity(acts):
+    """The previous-offset inputs of a batch as the network holds them."""
+    return acts[0][:, N_RES:D_IN]
+
+
 def loss(theta, X, Y, round_bf16=False):
-    O, _ = forward(theta, X, round_bf16)
-    return loss_and_grad_out(O, Y)[0]
+    O, acts = forward(theta, X, round_bf16)
+    return loss_and_grad_out(O, Y, velocity(acts))[0]
 
 
 def loss_and_grad(theta, X, Y, round_bf16=True):
     O, acts = forward(theta, X, round_bf16)
-    L, G = loss_and_grad_out(O, Y)
+    L, G = loss_and_grad_out(O, Y, velocity(acts))
     return L, backward(theta, acts, G, round_bf16), O
 
 
@@ -225,12 +237,14 @@ class Adam:
 
 
 # ----------------------------------------------------------------------------- proposal
-def proposal(o, pose_prev, kappa=2.0, r_min=(2e-3, 2e-3, 2e-3, 4e-3, 4e-3, 4e-3), r_max=(0.2, 0.2, 0.2, 0.4, 0.4, 0.4)):
-    """Initial swarm state of one frame from one network output o (>= 12 values):
-    c_0 = s*_{t-1} (+) (mu * units) and r_0 = clip(kappa * e^{clamp(s)} * units,
-    r_min, r_max) per axis (quaternion-vector axes first, then translation)."""
+def proposal(o, v, pose_prev, kappa=2.0, r_min=(2e-3, 2e-3, 2e-3, 4e-3, 4e-3, 4e-3),
+             r_max=(0.2, 0.2, 0.2, 0.4, 0.4, 0.4)):
+    """Initial swarm state of one frame from one network output o (>= 12 values)
+    and its previous-offset input v (6 values): c_0 = s*_{t-1} (+) (mu * units),
+    mu = v + o[0:6], and r_0 = clip(kappa * e^{clamp(s)} * units, r_min, r_max)
+    per axis (quaternion-vector axes first, then translation)."""
     o = np.asarray(o, np.float64)
-    delta = o[0:6] * OFFSET_UNITS
+    delta = (np.asarray(v, np.float64) + o[0:6]) * OFFSET_UNITS
     c0 = compose_offset(np.asarray(pose_prev, np.float64), delta)
     r0 = np.clip(kappa * np.exp(np.clip(o[6:12], -S_CLAMP, S_CLAMP)) * OFFSET_UNITS, r_min, r_max)
     return c0, r0

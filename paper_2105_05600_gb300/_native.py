@@ -159,7 +159,7 @@ def _load():
         "rf_proposal_features": (i, [P, P, ctypes.POINTER(rf_intrinsics), P, P, P, P]),
         "rf_proposal_target": (i, [P, P, P, P]),
         "rf_proposal_default_params": (None, [ctypes.POINTER(rf_proposal_params)]),
-        "rf_proposal_apply": (i, [P, P, ctypes.POINTER(rf_proposal_params), P, P, P]),
+        "rf_proposal_apply": (i, [P, P, P, ctypes.POINTER(rf_proposal_params), P, P, P]),
         "rf_learned_create": (i, [P, P, P, ctypes.POINTER(rf_proposal_params), i, i, ctypes.POINTER(P)]),
         "rf_learned_destroy": (None, [P]),
         "rf_learned_start": (i, [P, P, i, ctypes.POINTER(rf_intrinsics), ctypes.POINTER(rf_pose), P]),
@@ -694,13 +694,14 @@ def proposal_params(**kw) -> rf_proposal_params:
     return p
 
 
-def rf_proposal_apply(out_dev, pose_prev_dev, params: rf_proposal_params, stream=None):
-    """(c_0 float32[7], r_0 float32[6]) CUDA tensors from one network output."""
+def rf_proposal_apply(out_dev, x_dev, pose_prev_dev, params: rf_proposal_params, stream=None):
+    """(c_0 float32[7], r_0 float32[6]) CUDA tensors from one network output and
+    the input row it came from."""
     import torch
 
     c0 = torch.empty(7, dtype=torch.float32, device="cuda")
     r0 = torch.empty(6, dtype=torch.float32, device="cuda")
-    _check(lib.rf_proposal_apply(_dptr(out_dev, torch.float32), _dptr(pose_prev_dev, torch.float32),
+    _check(lib.rf_proposal_apply(_dptr(out_dev, torch.float32), _bf16_ptr(x_dev), _dptr(pose_prev_dev, torch.float32),
                                  ctypes.byref(params), _dptr(c0), _dptr(r0), _stream(stream)))
     return c0, r0
 

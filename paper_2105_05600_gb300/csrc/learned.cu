@@ -120,8 +120,9 @@ struct PropParams {
     float r_min[6], r_max[6];
 };
 
-// c_0 = s*_{t-1} (+) mu * units,  r_0 = clip(kappa e^s units, r_min, r_max).
-__device__ void proposal(const float *o, const float *prev, const PropParams &p, float *c0, float *r0)
+// c_0 = s*_{t-1} (+) mu * units with mu = x_v + o_mu (x_v: the previous-offset
+// inputs of the network), r_0 = clip(kappa e^s units, r_min, r_max).
+__device__ void proposal(const float *o, const bf16 *x, const float *prev, const PropParams &p, float *c0, float *r0)
 {
     Pose c;
     for (int a = 0; a < 4; ++a)
@@ -130,7 +131,7 @@ __device__ void proposal(const float *o, const float *prev, const PropParams &p,
         c.t[a] = prev[4 + a];
     float d[6];
     for (int i = 0; i < 6; ++i)
-        d[i] = o[i] * (float)c_units[i];
+        d[i] = (__bfloat162float(x[N_RES + i]) + o[i]) * (float)c_units[i];
     Pose out;
     compose_offset(c, d, false, out);
     for (int a = 0; a < 4; ++a)
@@ -143,9 +144,10 @@ __device__ void proposal(const float *o, const float *prev, const PropParams &p,
     }
 }
 
-__global__ void apply_kernel(const float *o, const float *prev, PropParams p, float *c0, float *r0, float *r0_copy)
+__global__ void apply_kernel(const float *o, const bf16 *x, const float *prev, PropParams p, float *c0, float *r0,
+                             float *r0_copy)
 {
-    proposal(o, prev, p, c0, r0);
+    proposal(o, x, prev, p, c0, r0);
     if (r0_copy)
         for (int i = 0; i < 6; ++i)
             r0_copy[i] = r0[i];
@@ -284,7 +286,8 @@ static rf_status learned_enqueue(rf_learned lp, const rf_intrinsics *K, rf_learn
     rf_status st = rf_mlp_forward(lp->net, lp->x, 1, lp->out, s);
     if (st != RF_OK)
         return st;
-    apply_kernel<<<1, 1, 0, s>>>(lp->out, S->hist[1], to_params(lp->p), S->c0, S->r_learned, S->r0);
+    apply_kernel<<<1, 1, 0, s>>>(lp->out, reinterpret_cast<const bf16 *>(lp->x), S->hist[1], to_params(lp->p), S->c0,
+                                 S->r_learned, S->r0);
     RF_CUDA(cudaGetLastError());
     rf_track_options o;
     memset(&o, 0, sizeof o);
@@ -348,15 +351,15 @@ rf_status rf_proposal_target(const float *pose_prev_dev, const float *pose_cur_d
     return RF_OK;
 }
 
-rf_status rf_proposal_apply(const float *out_dev, const float *pose_prev_dev, const rf_proposal_params *p,
-                            float *init_pose_dev, float *scale_dev, void *stream)
+rf_status rf_proposal_apply(const float *out_dev, const uint16_t *x_dev, const float *pose_prev_dev,
+                            const rf_proposal_params *p, float *init_pose_dev, float *scale_dev, void *stream)
 {
-    RF_CHECK_ARG(out_dev && pose_prev_dev && init_pose_dev && scale_dev, "null pointer");
+    RF_CHECK_ARG(out_dev && x_dev && pose_prev_dev && init_pose_dev && scale_dev, "null pointer");
     rf_status st = check_params(p);
     if (st != RF_OK)
         return st;
-    apply_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(out_dev, pose_prev_dev, to_params(*p), init_pose_dev, scale_dev,
-                                                    nullptr);
+    apply_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(out_dev, reinterpret_cast<const bf16 *>(x_dev), pose_prev_dev,
+                                                    to_params(*p), init_pose_dev, scale_dev, nullptr);
     RF_CUDA(cudaGetLastError());
     return RF_OK;
 }

@@ -403,11 +403,12 @@ __global__ void gather_kernel(const bf16 *x_all, const float *y_all, const int *
 }
 
 // Loss (mean over the batch of sum_d 1/2 r^2 (1 + e^{-2s}) + s, r = y - mu,
-// s = clamp(o_s, -6, 6)) and its gradient with respect to the 16 outputs,
+// mu = x_v + o_mu with x_v the previous-offset inputs (columns 768..773 of the
+// batch rows), s = clamp(o_s, -6, 6)) and its gradient with respect to the 16 outputs,
 // computed in FP32 per sample and stored as bfloat16 (row-major and
 // transposed) for the backward products; the batch sum runs in FP64 in a fixed
 // order.  One CTA, one thread per sample (B <= 1024).
-__global__ void loss_kernel(const float *out, const float *y, int B, bf16 *g, bf16 *gt, float *loss)
+__global__ void loss_kernel(const float *out, const float *y, const bf16 *x, int B, bf16 *g, bf16 *gt, float *loss)
 {
     __shared__ double red[32];
     const int b = threadIdx.x;
@@ -419,7 +420,8 @@ __global__ void loss_kernel(const float *out, const float *y, int B, bf16 *g, bf
         const float inv_b = 1.f / (float)B;
         float lf = 0.f;
         for (int d = 0; d < 6; ++d) {
-            const float mu = out[b * RF_MLP_OUT + d], sr = out[b * RF_MLP_OUT + 6 + d];
+            const float mu = out[b * RF_MLP_OUT + d] + __bfloat162float(x[(size_t)b * RF_MLP_IN + RF_MLP_IN_USED - 6 + d]);
+            const float sr = out[b * RF_MLP_OUT + 6 + d];
             const float s = fminf(fmaxf(sr, -6.f), 6.f);
             const float r = y[b * 6 + d] - mu;
             const float ex = expf(-2.f * s);
@@ -664,7 +666,7 @@ static rf_status mlp_gradient(rf_mlp m, const bf16 *x_all, const float *y_all, c
     rf_status st = mlp_forward(m, m->x, B, m->out, 1, s);
     if (st != RF_OK)
         return st;
-    loss_kernel<<<1, (B + 31) / 32 * 32, 0, s>>>(m->out, m->y, B, m->g, m->gt, m->loss);
+    loss_kernel<<<1, (B + 31) / 32 * 32, 0, s>>>(m->out, m->y, m->x, B, m->g, m->gt, m->loss);
     RF_CUDA(cudaGetLastError());
     // layer 4: dW4 = g^T h3, db4 = sum_b g, dH3 = g W4 masked by h3 > 0
     const bf16 *dA = m->g, *dAt = m->gt;

@@ -17,7 +17,7 @@ import numpy as np
 from . import metrics, synth
 
 LAYERS = [(256, 832), (256, 256), (256, 256), (16, 256)]  # (out, in) per layer
-N_USED_IN, N_USED_OUT = 774, 12
+N_RES, N_USED_IN, N_USED_OUT = 768, 774, 12
 
 
 # ----------------------------------------------------------------------------- inputs
@@ -122,9 +122,11 @@ def init_params(seed: int) -> np.ndarray:
 def train(nat, X, Y, train_rows, val_rows, epochs: int = 30, batch: int = 512, lr: float = 1e-3,
           lr_final: float = 2e-5, seed: int = 0):
     """Adam on the mean + log-scale loss over train_rows (cosine learning-rate
-    decay), validation loss on val_rows after every epoch; the network keeps the
-    parameters of the epoch with the lowest validation loss (early stopping).
-    Returns (MLP, history)."""
+    decay).  After every epoch the held-out rows give the loss and the squared
+    error of the predicted offset; the network keeps the parameters of the epoch
+    with the lowest offset error (the log-scale head overfits long before the
+    offset does, so the loss itself would stop too early), then its scale head is
+    calibrated on the held-out rows (calibrate_scale).  Returns (MLP, history)."""
     import torch
 
     net = nat.MLP(batch)
@@ -136,7 +138,7 @@ def train(nat, X, Y, train_rows, val_rows, epochs: int = 30, batch: int = 512, l
     per_epoch = len(train_rows) // batch
     total = epochs * per_epoch
     losses = torch.zeros(max(total, 1), dtype=torch.float32, device="cuda")
-    hist = dict(train=[], val=[])
+    hist = dict(train=[], val=[], val_offset_err=[])
     step = 0
     best, best_theta = float("inf"), None
     t0 = time.perf_counter()
@@ -149,18 +151,48 @@ def train(nat, X, Y, train_rows, val_rows, epochs: int = 30, batch: int = 512, l
             step += 1
         hist["train"].append(float(losses[step - per_epoch:step].mean().item()))
         hist["val"].append(validation_loss(net, X, Y, va_idx, batch))
-        if hist["val"][-1] < best:
-            best, best_theta = hist["val"][-1], net.get_params()
+        mu, _, Yv = predict(net, X, Y, va_idx, batch)
+        hist["val_offset_err"].append(float(((mu - Yv) ** 2).sum(1).mean().item()))
+        if hist["val_offset_err"][-1] < best:
+            best, best_theta = hist["val_offset_err"][-1], net.get_params()
             hist["best_epoch"] = ep
     torch.cuda.synchronize()
     hist["seconds"] = time.perf_counter() - t0
     hist["steps"] = step
     if best_theta is not None:
         net.set_params(best_theta)
+    hist["scale_calibration"] = calibrate_scale(net, X, Y, va_idx, batch)
+    hist["zero_offset_err"] = float((Y[va_idx.long()] ** 2).sum(1).mean().item())
     st = net.status()
     if st != 0:
         raise nat.RfError(st, "network kernels reported an error during training")
     return net, hist
+
+
+def predict(net, X, Y, idx, batch: int):
+    """(mean offset mu = previous offset + correction (rows, 6), network outputs
+    (rows, 16), targets (rows, 6)) of the dataset rows idx."""
+    import torch
+
+    outs = torch.cat([net.forward(X[idx[b:b + batch].long()].contiguous()) for b in range(0, len(idx), batch)])
+    v = X[idx.long()][:, N_RES:N_USED_IN].float()
+    return v + outs[:, :6], outs, Y[idx.long()]
+
+
+def calibrate_scale(net, X, Y, va_idx, batch: int):
+    """Per-axis scale calibration on held-out rows: with r = y - mu and the
+    predicted log scale s, k_d^2 = mean(r_d^2 e^{-2 s_d}) is the factor by which
+    the predicted variances are off; adding log k_d to the output bias of s_d
+    makes them match on those rows.  Returns the k_d."""
+    mu, O, Yv = predict(net, X, Y, va_idx, batch)
+    s = O[:, 6:12].clamp(-6.0, 6.0)
+    k2 = (((Yv - mu) ** 2) * (-2.0 * s).exp()).mean(0).double().cpu().numpy()
+    k = np.sqrt(np.maximum(k2, 1e-12))
+    theta = net.get_params()
+    b4 = sum(o * i + o for o, i in LAYERS[:3]) + LAYERS[3][0] * LAYERS[3][1]  # offset of b4
+    theta[b4 + 6:b4 + 12] += np.log(k).astype(np.float32)
+    net.set_params(theta)
+    return [float(v) for v in k]
 
 
 def validation_loss(net, X, Y, va_idx, batch: int) -> float:

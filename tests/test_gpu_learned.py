@@ -142,10 +142,11 @@ def test_learned_step_with_a_constant_proposal(oracle, nat, tiny):
     s = nat.learned_stats_dict(sb)
     assert status == 0 and s["status"] == 0
     assert s["used_fallback"] == 0 and s["chose_fallback"] == 0 and 1 <= s["iters_learned"] <= k_l
-    # the proposal: c_0 = s*_{t-1}, r_0 = kappa e^s units
+    # the proposal: c_0 = s*_{t-1} (no previous motion at the first frame, mu = 0),
+    # r_0 = kappa e^s units
     o = np.zeros(16)
     o[6:12] = np.float32(s_val)
-    c0, r0 = mlp.proposal(o, prev, kappa=2.0)
+    c0, r0 = mlp.proposal(o, np.zeros(6), prev, kappa=2.0)
     np.testing.assert_allclose(s["init_pose"], c0, atol=1e-6)
     np.testing.assert_allclose(s["r0"], r0, rtol=2e-6)
     # the short run is Algorithm 1 from that initialisation

@@ -39,10 +39,10 @@ def test_trained_proposal_beats_the_zero_offset_and_plain_pfo(nat):
     net, hist = learned.train(nat, ds["X"], ds["Y"], train_rows, val_rows, epochs=20, batch=256)
     assert net.status() == 0
     # proposal quality on the held-out sequences' samples
-    rows = torch.as_tensor(val_rows[:256].astype(np.int32), device="cuda")
-    o = net.forward(ds["X"][rows.long()].contiguous()).cpu().numpy()
-    y = ds["Y"][rows.long()].cpu().numpy()
-    err_net = np.mean(np.sum((o[:, :6] - y) ** 2, axis=1))
+    rows = torch.as_tensor(val_rows.astype(np.int32), device="cuda")
+    mu, _, y = learned.predict(net, ds["X"], ds["Y"], rows, 256)
+    mu, y = mu.cpu().numpy(), y.cpu().numpy()
+    err_net = np.mean(np.sum((mu - y) ** 2, axis=1))
     err_zero = np.mean(np.sum(y ** 2, axis=1))
     assert err_net < 0.8 * err_zero, (err_net, err_zero)
     # tracking A/B on one held-out sequence

@@ -143,7 +143,7 @@ def test_gradient_matches_oracle(nat):
     Y = (np.random.default_rng(5).normal(size=(B, 6)) * 0.5).astype(np.float32).astype(np.float64)
     L, g_or, O = mlp.loss_and_grad(theta, X, Y, round_bf16=True)
     _, acts = mlp.forward(theta, X, round_bf16=True)
-    Gm = magnitude_gradient(theta, acts, mlp.loss_and_grad_out(O, Y)[1])
+    Gm = magnitude_gradient(theta, acts, mlp.loss_and_grad_out(O, Y, mlp.velocity(acts))[1])
     net = nat.MLP(B)
     net.set_params(theta.astype(np.float32))
     grad, loss, out = net.gradient(to_bf16(X), torch.from_numpy(Y.astype(np.float32)).cuda(), B)
@@ -178,7 +178,7 @@ def test_gradient_with_index_gather(nat):
     np.testing.assert_array_equal(out.cpu().numpy().astype(np.float64), O)
     assert abs(float(loss.item()) - L) <= 1e-6 * abs(L)
     _, acts = mlp.forward(theta, X[idx], round_bf16=True)
-    Gm = magnitude_gradient(theta, acts, mlp.loss_and_grad_out(O, Y[idx])[1])
+    Gm = magnitude_gradient(theta, acts, mlp.loss_and_grad_out(O, Y[idx], mlp.velocity(acts))[1])
     assert np.all(np.abs(grad.cpu().numpy() - g_or) <= 4 * U * Gm + 1e-30)
     # an index outside the dataset is reported, not read
     bad = torch.from_numpy(np.r_[idx[:-1], n_all].astype(np.int32)).cuda()
@@ -196,7 +196,7 @@ def test_adam_first_step(nat):
     Y = np.random.default_rng(10).normal(size=(B, 6)).astype(np.float32).astype(np.float64)
     _, g_or, O = mlp.loss_and_grad(theta, X, Y, round_bf16=True)
     _, acts = mlp.forward(theta, X, round_bf16=True)
-    Gm = magnitude_gradient(theta, acts, mlp.loss_and_grad_out(O, Y)[1])
+    Gm = magnitude_gradient(theta, acts, mlp.loss_and_grad_out(O, Y, mlp.velocity(acts))[1])
     net = nat.MLP(B)
     net.set_params(theta.astype(np.float32))
     lr = 1e-3
@@ -316,8 +316,10 @@ def test_target_and_proposal_match_oracle(nat):
         o[:6] = rng.normal(size=6)
         o[6:12] = rng.uniform(-8, 3, size=6)  # some clamped at -6, some clipped at r_min / r_max
         p = nat.proposal_params(kappa=1.5)
-        c0, r0 = nat.rf_proposal_apply(torch.from_numpy(o).cuda(), tp, p)
-        oc, orr = mlp.proposal(o.astype(np.float64), prev, kappa=1.5)
+        x = np.zeros(832)
+        x[768:774] = mlp.bf16(rng.normal(size=6) * 0.5)  # previous offset: the base of mu
+        c0, r0 = nat.rf_proposal_apply(torch.from_numpy(o).cuda(), to_bf16(x), tp, p)
+        oc, orr = mlp.proposal(o.astype(np.float64), x[768:774], prev, kappa=1.5)
         c0 = c0.cpu().numpy()
         if np.dot(c0[:4], oc[:4]) < 0:
             c0[:4] = -c0[:4]

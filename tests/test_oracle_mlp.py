@@ -143,20 +143,28 @@ def test_loss_closed_forms():
     Y = np.random.default_rng(5).normal(size=(B, 6))
     O = np.zeros((B, 16))
     O[:, :6] = Y
-    L, G = mlp.loss_and_grad_out(O, Y)
+    V = np.zeros((B, 6))
+    L, G = mlp.loss_and_grad_out(O, Y, V)
     assert L == 0.0
     np.testing.assert_array_equal(G[:, :6], 0.0)
     np.testing.assert_allclose(G[:, 6:12], 1.0 / B)  # dL/ds = (1 - 0) / B
     O[:, :6] = Y - 1.0
     O[:, 6:12] = np.log(2.0)
-    L, G = mlp.loss_and_grad_out(O, Y)
+    L, G = mlp.loss_and_grad_out(O, Y, V)
     np.testing.assert_allclose(L, 6 * (0.5 * 1.0 * (1 + 0.25) + np.log(2.0)), rtol=1e-14)
     np.testing.assert_allclose(G[:, :6], -1.25 / B, rtol=1e-14)
     np.testing.assert_allclose(G[:, 6:12], (1 - 0.25) / B, rtol=1e-14)
     assert np.all(G[:, 12:] == 0.0)
     O[:, 6] = 7.0  # clamped: value uses s = 6, gradient is zero
-    L2, G2 = mlp.loss_and_grad_out(O, Y)
+    L2, G2 = mlp.loss_and_grad_out(O, Y, V)
     assert np.all(G2[:, 6] == 0.0)
+    # the mean is the previous offset plus the correction: shifting V by d and O
+    # by -d changes nothing
+    d = np.random.default_rng(6).normal(size=(B, 6))
+    O2 = O.copy()
+    O2[:, :6] -= d
+    L3, G3 = mlp.loss_and_grad_out(O2, Y, V + d)
+    assert L3 == pytest.approx(L2, rel=1e-12) and np.allclose(G3, G2, rtol=1e-12, atol=1e-15)
 
 
 @pytest.fixture(scope="module")
@@ -254,7 +262,7 @@ def test_adam_fits_a_linear_least_squares_problem():
 def test_proposal_of_a_zero_output_is_the_previous_pose():
     prev = np.array([0.9, 0.1, -0.3, 0.2, 1.0, 2.0, 0.5])
     prev[:4] /= np.linalg.norm(prev[:4])
-    c0, r0 = mlp.proposal(np.zeros(16), prev, kappa=2.0)
+    c0, r0 = mlp.proposal(np.zeros(16), np.zeros(6), prev, kappa=2.0)
     np.testing.assert_allclose(c0, prev, atol=1e-15)
     np.testing.assert_allclose(r0, 2.0 * mlp.OFFSET_UNITS)
 
@@ -263,9 +271,10 @@ def test_proposal_moves_by_the_predicted_offset():
     rng = np.random.default_rng(10)
     prev = rand_pose(rng)
     cur, d = small_step(rng, prev)
+    v = rng.normal(size=6) * 0.3  # previous offset; the network predicts the rest
     o = np.zeros(16)
-    o[:6] = mlp.target(prev, cur)
+    o[:6] = mlp.target(prev, cur) - v
     o[6:12] = np.log(0.01)  # tiny scale: clipped to r_min
-    c0, r0 = mlp.proposal(o, prev)
+    c0, r0 = mlp.proposal(o, v, prev)
     np.testing.assert_allclose(c0, cur, atol=1e-12)
     np.testing.assert_allclose(r0, [2e-3, 2e-3, 2e-3, 4e-3, 4e-3, 4e-3])

@@ -760,8 +760,8 @@ def run_mlp_bench(args):
 
 
 # ----------------------------------------------------------------------------- ablation flags
-ABLATIONS = [("full", 0), ("no_overlap", -1), ("no_normalize", -2), ("no_kahan", -4), ("nearest", 8),
-             ("rho_ref_centre", 16), ("se3_product", 64)]
+ABLATIONS = [("full", 0), ("no_overlap", -1), ("no_normalize", -2), ("no_kahan", -4), ("no_cell_margin", -128),
+             ("nearest", 8), ("rho_ref_centre", 16), ("se3_product", 64)]
 
 
 def run_ablation_bench(args):

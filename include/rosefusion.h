@@ -66,7 +66,8 @@ typedef struct {
 #define RF_RHO_REF_CENTER 16 /* APS threshold = fitness of the centre particle          */
 #define RF_L1 32             /* sum |psi| instead of psi^2                               */
 #define RF_RIGHT_MULT 64     /* particle offset applied in the camera frame              */
-#define RF_DEFAULT_FLAGS (RF_OVERLAP | RF_NORMALIZE | RF_COMPENSATED)
+#define RF_CELL_MARGIN 128   /* O_k: re-projection inside frame t-1 by one cell footprint */
+#define RF_DEFAULT_FLAGS (RF_OVERLAP | RF_NORMALIZE | RF_COMPENSATED | RF_CELL_MARGIN)
 
 /* Parameters of Algorithm 1; the defaults of the paper are tau = 1 (Sec. 3.2),
  * beta = 0.1 (Eq. momentum), eps = 1e-3 (Eq. rsinter), stop_eps = 1e-6 and
@@ -191,16 +192,21 @@ rf_status rf_depth_to_points(const float *depth_dev, const rf_intrinsics *K, int
  * rf_overlap_mask -- the overlap set of Eq. validness: point j (w != 0) is in
  * O if, moved to the world with pose_cur and into frame t-1 with pose_prev,
  * it lies in front of that camera, rounds to a pixel inside the image and
- * frame t-1's depth there is valid.
+ * frame t-1's depth there is valid.  With cell_extent > 0 its continuous
+ * pixel position (u, v) must also satisfy
+ *   fx c / z' - 1/2 <= u < W - 1/2 - fx c / z'   (and likewise v with fy, H),
+ * c = cell_extent in metres, z' the point's depth in frame t-1: the TSDF cell
+ * the point samples then lies inside frame t-1's view.  The tracker uses
+ * c = sqrt(3) voxels under RF_CELL_MARGIN; 0 gives the plain test.
  *   points_dev      device float4[m] (rf_depth_to_points layout)
  *   prev_depth_dev  device float[H * W], full resolution
  *   mask_dev        device uint8[m] (1 = in O)
  *   count_dev       device int[1] receiving |O| (may be NULL)
- * Asynchronous.
+ * Asynchronous.  RF_ERR_ARG for a negative or non-finite cell_extent.
  */
 rf_status rf_overlap_mask(const float *points_dev, int m, const float *prev_depth_dev, const rf_intrinsics *K,
-                          const rf_pose *pose_cur, const rf_pose *pose_prev, uint8_t *mask_dev, int *count_dev,
-                          void *stream);
+                          const rf_pose *pose_cur, const rf_pose *pose_prev, float cell_extent, uint8_t *mask_dev,
+                          int *count_dev, void *stream);
 
 /* ------------------------------------------------------------- fitness --- */
 /*

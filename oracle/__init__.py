@@ -32,8 +32,8 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "librf_oracle.so")
 _SRC = os.path.join(_HERE, "rf_oracle.c")
 
-OVERLAP, NORMALIZE, COMPENSATED, NEAREST, RHO_REF_CENTER, L1, RIGHT_MULT = 1, 2, 4, 8, 16, 32, 64
-DEFAULT_FLAGS = OVERLAP | NORMALIZE | COMPENSATED
+OVERLAP, NORMALIZE, COMPENSATED, NEAREST, RHO_REF_CENTER, L1, RIGHT_MULT, CELL_MARGIN = 1, 2, 4, 8, 16, 32, 64, 128
+DEFAULT_FLAGS = OVERLAP | NORMALIZE | COMPENSATED | CELL_MARGIN
 TRACE_STRIDE = 40
 QMODE = {"f64": 0, "f32": 1, "f16": 2, "i16": 3}
 
@@ -68,7 +68,7 @@ def _load():
             lib.or_particle_pose.argtypes = [D, D, D, i, D]
             lib.or_unproject.argtypes = [F, i, i, d, d, d, d, d, d, i, D]
             lib.or_unproject.restype = i
-            lib.or_overlap.argtypes = [D, i, F, i, i, d, d, d, d, d, d, D, D, I, D]
+            lib.or_overlap.argtypes = [D, i, F, i, i, d, d, d, d, d, d, D, D, d, I, D]
             lib.or_overlap.restype = i
             lib.or_tsdf_sample.argtypes = [D, I, d, D, D, i, D]
             lib.or_tsdf_sample.restype = i
@@ -167,8 +167,9 @@ def unproject(depth, K, stride):
     return pts
 
 
-def overlap(pts, prev_depth, K, pose_cur, pose_prev):
-    """Eq. validness mask and rounding margins for every point."""
+def overlap(pts, prev_depth, K, pose_cur, pose_prev, cell_m=0.0):
+    """Eq. validness mask and rounding margins for every point; cell_m > 0 also
+    keeps the re-projection fx cell_m / z' pixels inside frame t-1's image."""
     lib = _load()
     pts, pp = _d(pts)
     prev_depth, pdp = _f(prev_depth)
@@ -179,7 +180,7 @@ def overlap(pts, prev_depth, K, pose_cur, pose_prev):
     mask, pm = _i(np.zeros(M, np.int32))
     margin, pmg = _d(np.zeros(M))
     n = lib.or_overlap(pp, M, pdp, W, H, K["fx"], K["fy"], K["cx"], K["cy"], K["z_min"], K["z_max"], ppc, ppv,
-                       pm, pmg)
+                       float(cell_m), pm, pmg)
     return mask, margin, n
 
 

@@ -28,6 +28,8 @@
  *  16 RHO_REF_CENTER  APS threshold = fitness of the current centre particle
  *  32 L1           sum |psi| instead of psi^2
  *  64 RIGHT_MULT   particle offset applied in the camera frame (T_c * T_delta)
+ * 128 CELL_MARGIN  overlap set: the re-projected point must lie inside frame
+ *                  t-1's image by the footprint of one TSDF cell (sqrt(3) voxels)
  *
  * Functions whose result has no independent pin say so in their comment;
  * every other function is pinned by tests/test_oracle_*.py.
@@ -44,6 +46,7 @@
 #define OR_RHO_REF_CENTER 16
 #define OR_L1 32
 #define OR_RIGHT_MULT 64
+#define OR_CELL_MARGIN 128
 
 #define OR_OK 0
 #define OR_ERR_ARG -1
@@ -189,14 +192,20 @@ int or_unproject(const float *depth, int W, int H, double fx, double fy, double 
  * is unprojected with the current estimate s*_{k-1}, re-projected into frame
  * t-1 with its final pose, and kept if it lands in front of that camera, the
  * nearest pixel lies inside the image and frame t-1 has a valid depth there.
+ * With cell_m > 0 (flag CELL_MARGIN, cell_m = sqrt(3) voxels) the continuous
+ * pixel position must also lie at least fx cell_m / z' (fy cell_m / z'
+ * vertically) pixels inside the image edges (-0.5 and W - 0.5), z' the
+ * point's depth in frame t-1: the TSDF cell the point samples then lies
+ * inside that frame's view, i.e. the pixel is observed by both frames at the
+ * volume's resolution.
  * margin[j] (optional) is the distance of the continuous pixel coordinate to
- * the nearest rounding boundary or image border (in pixels); tests use it to
- * skip decisions that FP32 and FP64 may legitimately take differently.
+ * the nearest rounding boundary or (inset) image border, in pixels; tests use
+ * it to skip decisions that FP32 and FP64 may legitimately take differently.
  * Returns |O_k|.
  */
 int or_overlap(const double *pts, int M, const float *prev_depth, int W, int H, double fx, double fy,
                double cx, double cy, double z_min, double z_max, const double pose_cur[7],
-               const double pose_prev[7], int *mask, double *margin)
+               const double pose_prev[7], double cell_m, int *mask, double *margin)
 {
     double Rc[9], Rp[9];
     or_quat_to_rot(pose_cur, Rc);
@@ -217,13 +226,20 @@ int or_overlap(const double *pts, int M, const float *prev_depth, int W, int H, 
         double u = fx * pc[0] / pc[2] + cx;
         double v = fy * pc[1] / pc[2] + cy;
         double ur = floor(u + 0.5), vr = floor(v + 0.5);
+        double bu = fx * cell_m / pc[2], bv = fy * cell_m / pc[2]; /* cell footprint in pixels */
         if (margin) {
             double mu = fabs((u + 0.5) - ur), mu2 = fabs((u + 0.5) - (ur + 1.0));
             double mv = fabs((v + 0.5) - vr), mv2 = fabs((v + 0.5) - (vr + 1.0));
             double m = fmin(fmin(mu, mu2), fmin(mv, mv2));
+            if (cell_m > 0.0) {
+                m = fmin(m, fmin(fabs(u - (bu - 0.5)), fabs(((double)W - 0.5 - bu) - u)));
+                m = fmin(m, fmin(fabs(v - (bv - 0.5)), fabs(((double)H - 0.5 - bv) - v)));
+            }
             margin[j] = m;
         }
         if (ur < 0.0 || ur >= (double)W || vr < 0.0 || vr >= (double)H)
+            continue;
+        if (u < bu - 0.5 || u >= (double)W - 0.5 - bu || v < bv - 0.5 || v >= (double)H - 0.5 - bv)
             continue;
         double d = prev_depth[(size_t)vr * W + (size_t)ur];
         if (d > z_min && d <= z_max) {
@@ -439,7 +455,8 @@ int or_pfo_frame(const double *F, const int dim[3], double voxel, const double o
         int nO = 0;
         double min_margin = INFINITY;
         if (flags & OR_OVERLAP) {
-            nO = or_overlap(pts, M, prev_depth, W, H, fx, fy, cx, cy, z_min, z_max, c, pose_prev, mask, margin);
+            nO = or_overlap(pts, M, prev_depth, W, H, fx, fy, cx, cy, z_min, z_max, c, pose_prev,
+                            (flags & OR_CELL_MARGIN) ? sqrt(3.0) * voxel : 0.0, mask, margin);
             for (int j = 0; j < M; ++j)
                 if (pts[4 * (size_t)j + 3] != 0.0 && margin[j] < min_margin)
                     min_margin = margin[j];
@@ -968,7 +985,8 @@ int or_pfo_frame_sched(const double *F, const int dim[3], double voxel, const do
         int nO = 0;
         double min_margin = INFINITY;
         if (flags & OR_OVERLAP) {
-            nO = or_overlap(pts, M, prev_depth, W, H, fx, fy, cx, cy, z_min, z_max, c, pose_prev, mask, margin);
+            nO = or_overlap(pts, M, prev_depth, W, H, fx, fy, cx, cy, z_min, z_max, c, pose_prev,
+                            (flags & OR_CELL_MARGIN) ? sqrt(3.0) * voxel : 0.0, mask, margin);
             for (int j = 0; j < M; ++j)
                 if (pts[4 * (size_t)j + 3] != 0.0 && margin[j] < min_margin)
                     min_margin = margin[j];

@@ -12,11 +12,11 @@ from __future__ import annotations
 
 import importlib
 
-__all__ = ["synth", "metrics", "build"]
+__all__ = ["synth", "metrics", "build", "learned"]
 
 
 def __getattr__(name):
-    if name in ("synth", "metrics", "build"):
+    if name in ("synth", "metrics", "build", "learned"):
         return importlib.import_module(f"{__name__}.{name}")
     native = importlib.import_module(f"{__name__}._native")
     try:

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "librosefusion.so")
 
 RF_OK, RF_ERR_ARG, RF_ERR_CUDA, RF_ERR_TIMEOUT, RF_ERR_EMPTY, RF_ERR_NOMEM = 0, -1, -2, -3, -4, -5
 RF_OVERLAP, RF_NORMALIZE, RF_COMPENSATED, RF_NEAREST, RF_RHO_REF_CENTER, RF_L1, RF_RIGHT_MULT = 1, 2, 4, 8, 16, 32, 64
-RF_DEFAULT_FLAGS = RF_OVERLAP | RF_NORMALIZE | RF_COMPENSATED
+RF_CELL_MARGIN = 128
+RF_DEFAULT_FLAGS = RF_OVERLAP | RF_NORMALIZE | RF_COMPENSATED | RF_CELL_MARGIN
 RF_MAX_ITERS = 64
 DTYPES = {"f32": 0, "f16": 1, "i16": 2}
 
@@ -118,7 +119,7 @@ def _load():
         "tsdf_integrate_dev": (i, [P, P, ctypes.POINTER(rf_intrinsics), P, P, P]),
         "rf_depth_to_points": (i, [P, ctypes.POINTER(rf_intrinsics), i, P, P]),
         "rf_overlap_mask": (i, [P, i, P, ctypes.POINTER(rf_intrinsics), ctypes.POINTER(rf_pose),
-                                ctypes.POINTER(rf_pose), P, P, P]),
+                                ctypes.POINTER(rf_pose), f, P, P, P]),
         "fitness_eval": (i, [P, P, i, P, i, ctypes.POINTER(rf_pose), ctypes.POINTER(f), ctypes.POINTER(rf_params),
                              P, P, P, P]),
         "fitness_eval_noalloc": (i, [P, P, i, P, i, ctypes.POINTER(rf_pose), ctypes.POINTER(f),
@@ -337,7 +338,8 @@ def rf_depth_to_points(depth, K: dict, stride: int, out=None, stream=None):
     return out
 
 
-def rf_overlap_mask(points, prev_depth, K: dict, pose_cur, pose_prev, stream=None):
+def rf_overlap_mask(points, prev_depth, K: dict, pose_cur, pose_prev, cell_extent=0.0, stream=None):
+    """(mask uint8[m], count int32[1]); cell_extent (metres) > 0 adds the cell-footprint inset."""
     import torch
 
     m = points.shape[0]
@@ -346,8 +348,8 @@ def rf_overlap_mask(points, prev_depth, K: dict, pose_cur, pose_prev, stream=Non
     Ki = make_intrinsics(K)
     pc, pp = make_pose(pose_cur), make_pose(pose_prev)
     _check(lib.rf_overlap_mask(_dptr(points, torch.float32), int(m), _dptr(prev_depth, torch.float32),
-                               ctypes.byref(Ki), ctypes.byref(pc), ctypes.byref(pp), _dptr(mask), _dptr(count),
-                               _stream(stream)))
+                               ctypes.byref(Ki), ctypes.byref(pc), ctypes.byref(pp), float(cell_extent), _dptr(mask),
+                               _dptr(count), _stream(stream)))
     return mask[:m], count
 
 

@@ -58,8 +58,12 @@ __device__ __forceinline__ void unproject_point(const float *__restrict__ depth,
 
 // Eq. validness for one point: world with the current estimate (Rc, tc), back
 // into frame t-1 with its final pose (Rp, tp), nearest pixel, valid depth.
+// cell_m > 0 (RF_CELL_MARGIN: sqrt(3) voxels) also keeps the continuous pixel
+// position fx cell_m / z' pixels inside the image edges, so that the TSDF cell
+// the point samples lies inside frame t-1's view.
 __device__ __forceinline__ bool overlap_test(const float4 &p, const float Rc[9], const float tc[3], const float Rp[9],
-                                             const float tp[3], const float *__restrict__ prev_depth, const Intr &K)
+                                             const float tp[3], const float *__restrict__ prev_depth, const Intr &K,
+                                             float cell_m)
 {
     if (p.w == 0.f)
         return false;
@@ -71,11 +75,16 @@ __device__ __forceinline__ bool overlap_test(const float4 &p, const float Rc[9],
     const float cz = Rp[2] * gx + Rp[5] * gy + Rp[8] * gz;
     if (!(cz > 0.f))
         return false;
-    const float u = floorf(K.fx * cx / cz + K.cx + 0.5f);
-    const float v = floorf(K.fy * cy / cz + K.cy + 0.5f);
+    const float uc = K.fx * cx / cz + K.cx, vc = K.fy * cy / cz + K.cy;
+    const float mu = K.fx * cell_m / cz, mv = K.fy * cell_m / cz;
+    if (!(uc >= mu - 0.5f && uc < (float)K.width - 0.5f - mu && vc >= mv - 0.5f && vc < (float)K.height - 0.5f - mv))
+        return false;
+    const float u = floorf(uc + 0.5f);
+    const float v = floorf(vc + 0.5f);
     if (!(u >= 0.f && u < (float)K.width && v >= 0.f && v < (float)K.height))
         return false;
-    return depth_valid(__ldg(&prev_depth[(size_t)v * K.width + (size_t)u]), K);
+    const float d = __ldg(&prev_depth[(size_t)v * K.width + (size_t)u]);
+    return depth_valid(d, K);
 }
 
 // ------------------------------------------------------------------ fitness (warp level)

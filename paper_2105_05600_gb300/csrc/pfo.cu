@@ -280,12 +280,13 @@ __global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kern
                     quat_rot(st[p].c.q, Rc);
                     quat_rot(st[p].prev.q, Rp);
                     const bool overlap_on = (pd.flags & RF_OVERLAP) != 0;
+                    const float cell_m = (pd.flags & RF_CELL_MARGIN) ? 1.7320508f * pd.V.voxel : 0.f;
                     for (int j0 = lo; j0 < hi; j0 += blockDim.x) {
                         const int j = j0 + tid;
                         int f = 0;
                         if (j < hi) {
                             const float4 pt = __ldcg(&pd.pts[st[p].off_lvl + (j - base)]);
-                            f = overlap_on ? overlap_test(pt, Rc, st[p].c.t, Rp, st[p].prev.t, pd.prev_depth, pd.K)
+                            f = overlap_on ? overlap_test(pt, Rc, st[p].c.t, Rp, st[p].prev.t, pd.prev_depth, pd.K, cell_m)
                                            : (pt.w != 0.f);
                         }
                         int tot;
@@ -349,6 +350,7 @@ __global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kern
                     quat_rot(st[p].c.q, Rc);
                     quat_rot(st[p].prev.q, Rp);
                     const bool overlap_on = (pd.flags & RF_OVERLAP) != 0;
+                    const float cell_m = (pd.flags & RF_CELL_MARGIN) ? 1.7320508f * pd.V.voxel : 0.f;
                     int out = st[p].offset;
                     for (int j0 = lo; j0 < hi; j0 += blockDim.x) {
                         const int j = j0 + tid;
@@ -356,7 +358,7 @@ __global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kern
                         float4 pt = make_float4(0.f, 0.f, 0.f, 0.f);
                         if (j < hi) {
                             pt = __ldcg(&pd.pts[st[p].off_lvl + (j - base)]);
-                            f = overlap_on ? overlap_test(pt, Rc, st[p].c.t, Rp, st[p].prev.t, pd.prev_depth, pd.K)
+                            f = overlap_on ? overlap_test(pt, Rc, st[p].c.t, Rp, st[p].prev.t, pd.prev_depth, pd.K, cell_m)
                                            : (pt.w != 0.f);
                         }
                         int tot;

@@ -58,7 +58,7 @@ __global__ void depth_to_points_kernel(const float *depth, Intr K, int stride, i
 }
 
 __global__ void overlap_kernel(const float4 *pts, int m, const float *prev_depth, Intr K, Pose cur, Pose prev,
-                               uint8_t *mask, int *count)
+                               float cell_m, uint8_t *mask, int *count)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     float Rc[9], Rp[9];
@@ -66,7 +66,7 @@ __global__ void overlap_kernel(const float4 *pts, int m, const float *prev_depth
     quat_rot(prev.q, Rp);
     bool in = false;
     if (j < m) {
-        in = overlap_test(pts[j], Rc, cur.t, Rp, prev.t, prev_depth, K);
+        in = overlap_test(pts[j], Rc, cur.t, Rp, prev.t, prev_depth, K, cell_m);
         mask[j] = in ? 1 : 0;
     }
     if (count) {
@@ -119,18 +119,20 @@ rf_status rf_depth_to_points(const float *depth_dev, const rf_intrinsics *K, int
 }
 
 rf_status rf_overlap_mask(const float *points_dev, int m, const float *prev_depth_dev, const rf_intrinsics *K,
-                          const rf_pose *pose_cur, const rf_pose *pose_prev, uint8_t *mask_dev, int *count_dev,
-                          void *stream)
+                          const rf_pose *pose_cur, const rf_pose *pose_prev, float cell_extent, uint8_t *mask_dev,
+                          int *count_dev, void *stream)
 {
     RF_CHECK_ARG(points_dev && prev_depth_dev && K && pose_cur && pose_prev && mask_dev, "null pointer");
     RF_CHECK_ARG(m >= 0, "negative size");
+    RF_CHECK_ARG(cell_extent >= 0.f && isfinite(cell_extent), "cell_extent must be finite and >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     if (count_dev)
         RF_CUDA(cudaMemsetAsync(count_dev, 0, sizeof(int), s));
     if (m == 0)
         return RF_OK;
     overlap_kernel<<<(m + 255) / 256, 256, 0, s>>>((const float4 *)points_dev, m, prev_depth_dev, to_intr(*K),
-                                                   to_pose(*pose_cur), to_pose(*pose_prev), mask_dev, count_dev);
+                                                   to_pose(*pose_cur), to_pose(*pose_prev), cell_extent, mask_dev,
+                                                   count_dev);
     RF_CUDA(cudaGetLastError());
     return RF_OK;
 }

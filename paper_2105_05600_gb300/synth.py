@@ -273,12 +273,20 @@ def render_depth_batch(scene: Scene, poses, K: dict, seed: int, noise: bool = Tr
 
 # --------------------------------------------------------------------------- trajectories
 def make_trajectory(scene: Scene, n_frames: int, speed: float, ang_speed: float, seed: int,
-                    fps: float = 30.0, walk_sigma: float = 0.05) -> np.ndarray:
+                    fps: float = 30.0, walk_sigma: float = 0.05, scan_gain: float = 3.0) -> np.ndarray:
     """(n_frames, 7) camera->world poses at constant linear speed (m/s) and
     angular speed (rad/s); the direction and the rotation axis follow smooth
     seeded random walks (walk_sigma per frame); the path reflects off planes
     `margin` inside the walls (camera_margin) and off spheres.  Rendering the
-    same motion statistics at k x fps takes walk_sigma / sqrt(k)."""
+    same motion statistics at k x fps takes walk_sigma / sqrt(k).
+
+    Scanning: each frame's rotation axis is the random-walk axis plus
+    scan_gain * (z_cam x (room centre - position)) (metres), which turns the
+    optical axis back towards the room's interior the further the camera is
+    from the centre, as a hand-held scan of a room does; a camera staring at
+    one flat wall from close by is the failure case the paper names for any
+    purely geometric tracker (Sec. 5.6).  scan_gain = 0 gives the plain random
+    walk starting at the room centre."""
     rng = np.random.default_rng(20_000 + seed)
     margin = camera_margin(scene)
     lo, hi = scene.lo + margin, scene.hi - margin
@@ -287,9 +295,11 @@ def make_trajectory(scene: Scene, n_frames: int, speed: float, ang_speed: float,
     def free(p):
         return all(np.linalg.norm(p - c) > r + 0.5 for c, r in zip(scene.centres, scene.radii))
 
+    # start in the camera's box, clear of the spheres and (when scanning) at least
+    # 1 m from the room centre, so that the first frames already look across the room
     p = centre.copy()
     for _ in range(1000):
-        if free(p):
+        if free(p) and (scan_gain == 0.0 or np.linalg.norm(p - centre) >= min(1.0, 0.5 * float((hi - lo).min()))):
             break
         p = rng.uniform(lo, hi)
     d = rng.normal(size=3)
@@ -317,7 +327,8 @@ def make_trajectory(scene: Scene, n_frames: int, speed: float, ang_speed: float,
         p = np.clip(p + speed * dt * d, lo, hi)
         axis = axis + rng.normal(size=3) * walk_sigma
         axis /= np.linalg.norm(axis)
-        q = _qcanon(_qmul(axis_angle_quat(axis, ang_speed * dt), q))
+        turn = axis + scan_gain * np.cross(_qrot(q)[:, 2], centre - out[f, 4:])
+        q = _qcanon(_qmul(axis_angle_quat(turn, ang_speed * dt), q))
     return out
 
 

@@ -111,3 +111,20 @@ def test_proposal_argument_errors_need_no_gpu(built_lib):
     o = n.rf_track_options(None, None, None, n.RF_MAX_ITERS + 1, 0)
     assert n.lib.pfo_track_frame_ex_async(None, None, None, None, None, None, None, ctypes.byref(o),
                                           None) == n.RF_ERR_ARG
+
+
+def test_binding_constants_match_the_header(built_lib):
+    # flag bits, error codes and size limits of the binding equal the header's #defines
+    from paper_2105_05600_gb300 import _native as n
+
+    src = open(os.path.join(INCLUDE, "rosefusion.h")).read()
+    defs = dict(re.findall(r"^#define\s+(RF_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", src, re.M))
+    assert "RF_CELL_MARGIN" in defs
+    checked = 0
+    for name, val in defs.items():
+        if hasattr(n, name):
+            assert getattr(n, name) == int(val), name
+            checked += 1
+    assert checked >= 12
+    combo = re.search(r"#define RF_DEFAULT_FLAGS \(([^)]*)\)", src).group(1)
+    assert n.RF_DEFAULT_FLAGS == sum(int(defs[t.strip()]) for t in combo.split("|"))

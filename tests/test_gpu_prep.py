@@ -61,7 +61,8 @@ def test_depth_to_points_parity(oracle, nat, W, H, stride):
     np.testing.assert_allclose(got[:, :3], ref[:, :3], rtol=1e-6, atol=1e-7)
 
 
-def test_overlap_parity(oracle, nat):
+@pytest.mark.parametrize("cell", [0.0, 0.01 * 3 ** 0.5])
+def test_overlap_parity(oracle, nat, cell):
     import torch
 
     cfg = synth.CONFIGS["paper"]
@@ -73,9 +74,9 @@ def test_overlap_parity(oracle, nat):
     pts = oracle.unproject(d1, K, 4).astype(np.float32).astype(np.float64)
     cur = traj[1].astype(np.float32).astype(np.float64)
     prev = traj[0].astype(np.float32).astype(np.float64)
-    mask, margin, n = oracle.overlap(pts, d0, K, cur, prev)
+    mask, margin, n = oracle.overlap(pts, d0, K, cur, prev, cell_m=cell)
     gmask, gcount = nat.rf_overlap_mask(torch.from_numpy(pts.astype(np.float32)).cuda(), torch.from_numpy(d0).cuda(),
-                                        K, cur, prev)
+                                        K, cur, prev, cell_extent=cell)
     gmask = gmask.cpu().numpy().astype(np.int32)
     sure = margin > 1e-3  # decisions more than 1e-3 px from a rounding boundary are unique
     assert sure.mean() > 0.99

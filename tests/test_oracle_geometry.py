@@ -153,6 +153,28 @@ def test_overlap_translation_shift(oracle):
     assert np.all(mask2[u == 13] == 0) and np.all(mask2[u == 14] == 1)
 
 
+def test_overlap_cell_margin_hand_count(oracle):
+    # cell_m = 0.225 m at z = 2 m and fx = fy = 20 px: a footprint of 2.25 px, so
+    # u must lie in [1.75, 40 - 0.5 - 2.25) -> columns 2..37 (36), rows 2..27 (26)
+    K, depth = _plane_frame()
+    pts = oracle.unproject(depth, K, 1)
+    I = np.array([1, 0, 0, 0, 0, 0, 0], float)
+    mask, margin, n = oracle.overlap(pts, depth, K, I, I, cell_m=0.225)
+    assert n == 36 * 26
+    u, v = np.arange(len(pts)) % 40, np.arange(len(pts)) // 40
+    assert np.array_equal(mask.astype(bool), (u >= 2) & (u <= 37) & (v >= 2) & (v <= 27))
+    assert np.min(margin) == pytest.approx(0.25)  # u = 2 lies 0.25 px inside the inset edge 1.75
+    # at z = 4 m the footprint halves (1.125 px): columns 1..38, rows 1..28
+    K4, d4 = _plane_frame(z=4.0)
+    p4 = oracle.unproject(d4, K4, 1)
+    assert oracle.overlap(p4, d4, K4, I, I, cell_m=0.225)[2] == 38 * 28
+    # with the 0.3 m shift of the previous camera (3 px), u - 3 must lie in [1.75, 37.25): columns 5..39
+    prev = np.array([1, 0, 0, 0, 0.3, 0, 0], float)
+    mask, _, n = oracle.overlap(pts, depth, K, I, prev, cell_m=0.225)
+    assert n == 35 * 26
+    assert np.all(mask[(u == 4)] == 0) and np.all(mask[(u == 5) & (v == 10)] == 1)
+
+
 def test_overlap_behind_previous_camera(oracle):
     K, depth = _plane_frame()
     pts = oracle.unproject(depth, K, 1)

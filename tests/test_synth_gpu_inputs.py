@@ -40,3 +40,27 @@ def test_substep_trajectory_keeps_the_motion_statistics():
     s30 = np.linalg.norm(np.diff(t30[:, 4:], axis=0), axis=1)
     s60 = np.linalg.norm(np.diff(t60[::2, 4:], axis=0), axis=1)
     assert abs(np.median(s30) - 2.0 / 30) < 2e-3 and abs(np.median(s60) - 2.0 / 30) < 4e-3
+
+
+def test_trajectory_speeds_and_scanning():
+    # every frame turns by exactly ang_speed / fps and moves by speed / fps (unless
+    # clipped at the camera box); the scanning bias keeps the optical axis on the
+    # room's interior: the camera looks towards the centre far more often than a
+    # plain random walk of the same seed, and stays inside the camera box
+    scene = synth.make_scene(5.12, 0.2, 11)
+    m = synth.camera_margin(scene)
+    centre = 0.5 * (scene.lo + scene.hi)
+    facing = {}
+    for gain in (0.0, 3.0):
+        tr = synth.make_trajectory(scene, 400, 2.0, 1.5, 11, scan_gain=gain)
+        dq = np.abs(np.sum(tr[1:, :4] * tr[:-1, :4], axis=1))
+        np.testing.assert_allclose(2 * np.arccos(np.minimum(1.0, dq)), 1.5 / 30, rtol=1e-6, atol=1e-7)
+        step = np.linalg.norm(np.diff(tr[:, 4:], axis=0), axis=1)
+        assert np.all(step <= 2.0 / 30 + 1e-12) and np.median(step) == pytest.approx(2.0 / 30)
+        assert np.all(tr[:, 4:] >= scene.lo + m - 1e-12) and np.all(tr[:, 4:] <= scene.hi - m + 1e-12)
+        z = np.stack([synth._qrot(q)[:, 2] for q in tr[:, :4]])
+        to = centre - tr[:, 4:]
+        far = np.linalg.norm(to, axis=1) > 0.5
+        cosang = np.sum(z[far] * to[far], axis=1) / np.linalg.norm(to[far], axis=1)
+        facing[gain] = float(np.mean(cosang > 0.0))
+    assert facing[3.0] > 0.9 and facing[3.0] > facing[0.0] + 0.2

@@ -426,7 +426,8 @@ int or_pst_update(int N, const double *rho, const double *delta, double rho_ref,
  * (r_1, handed to the next frame), the trace, the number of iterations.
  * Loop order follows Algorithm 1 with the readings: iteration k evaluates the
  * PST centred at c_{k-1} with axes r_{k-1}; rho_ref = rho of particle 0 at
- * k = 1 (and with RHO_REF_CENTER), else the carried Eq. wafit value; stop on
+ * k = 1 (and with RHO_REF_CENTER), else the carried Eq. wafit value; the APS
+ * is drawn from particles 1..N-1 (particle 0 is s*_{k-1} itself); stop on
  * two consecutive empty APS, a step below stop_eps in all six dimensions, or
  * k = k_max (Sec. 4 "Convergence criteria").
  * Returns 0, or OR_ERR_EMPTY if |O_k| = 0 (the pose then stays s*_{k-1}).
@@ -502,7 +503,10 @@ int or_pfo_frame(const double *F, const int dim[3], double voxel, const double o
             if (fabs(rho[i] - rho_ref) < min_gap && i != 0)
                 min_gap = fabs(rho[i] - rho_ref);
         double dbar[6], rho_tilde, r_new[6];
-        int n_aps = or_pst_update(N, rho, delta, rho_ref, r, beta, eps, dbar, &rho_tilde, r_new);
+        /* the APS holds particles better than s*_{k-1}; particle 0 (zero offset) is
+         * s*_{k-1} itself, so it is no candidate (it only passes rho_ref when that is
+         * the Eq. wafit approximation) */
+        int n_aps = or_pst_update(N - 1, rho + 1, delta + 6, rho_ref, r, beta, eps, dbar, &rho_tilde, r_new);
         double s_new[7];
         if (n_aps > 0) {
             or_compose_offset(c, dbar, flags, s_new);
@@ -1030,7 +1034,7 @@ int or_pfo_frame_sched(const double *F, const int dim[3], double voxel, const do
             if (fabs(rho[i] - rho_ref) < min_gap)
                 min_gap = fabs(rho[i] - rho_ref);
         double dbar[6], rho_tilde, r_new[6];
-        int n_aps = or_pst_update(Nl, rho, delta, rho_ref, r, beta, eps, dbar, &rho_tilde, r_new);
+        int n_aps = or_pst_update(Nl - 1, rho + 1, delta + 6, rho_ref, r, beta, eps, dbar, &rho_tilde, r_new);
         double s_new[7];
         if (n_aps > 0) {
             or_compose_offset(c, dbar, flags, s_new);

@@ -464,7 +464,8 @@ __global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kern
                 particle_total(pd.part_S, pd.part_n, st[p].n_lvl, st[p].n_chunks, i, true, S, nv);
                 const float rho = fitness_rho(S, st[p].nO, pd.tau, normalize);
                 merge_max(rmax, amax, r2, rho, i, -1.f);
-                if (rho > rho_ref) {
+                // particle 0 is the centre s*_{k-1} itself: never a member of the APS
+                if (i > 0 && rho > rho_ref) {
                     const double wgt = (double)(rho - rho_ref);
                     ++naps;
                     sw += wgt;

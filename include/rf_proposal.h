@@ -126,6 +126,11 @@ typedef struct {
                         theta < 0: never (default 0.9) */
     float r_min[6];  /* default 2e-3 (rotation axes), 4e-3 m (translation) */
     float r_max[6];  /* default 0.2, 0.4 m */
+    int resume;      /* 1 (default): when the learned run used all k_learned
+                        iterations without meeting a convergence criterion of
+                        Sec. 4 (and the fallback rule did not fire), PFO resumes
+                        from its s* and axis lengths for up to k_fallback more
+                        iterations; 0: no second run in that case */
 } rf_proposal_params;
 
 /* Fills *p with the defaults above. */
@@ -149,15 +154,17 @@ rf_status rf_proposal_apply(const float *out_dev, const uint16_t *x_dev, const f
  *   proposal (c_0, r_0) -> PFO with at most k_learned iterations from c_0
  *   (pfo_track_frame_ex_async; the overlap set still uses s*_{t-1}) -> if the
  *   fallback rule fires, plain PFO from s*_{t-1} with the carried r_1 and
- *   k_fallback iterations; the result with the higher final rho_tilde is kept
- *   -> fusion (tsdf_integrate) of D_t at the kept pose.
+ *   k_fallback iterations; else, with `resume`, if the learned run stopped at
+ *   k_learned unconverged, PFO continues from its s* and axis lengths for up
+ *   to k_fallback iterations; the result with the higher final rho_tilde is
+ *   kept -> fusion (tsdf_integrate) of D_t at the kept pose.
  * Frames are at most max_width x max_height.  The tracker and network must not
  * be used by other calls while a step runs.
  */
 typedef struct rf_learned_s *rf_learned;
 typedef struct {
     int status;          /* final status of the frame (0 = OK) */
-    int used_fallback;   /* the fallback run happened */
+    int used_fallback;   /* second run: 0 none, 1 plain restart, 2 resumed */
     int chose_fallback;  /* its result was kept */
     int iters_learned;
     int iters_fallback;

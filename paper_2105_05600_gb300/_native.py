@@ -71,7 +71,8 @@ class rf_track_options(ctypes.Structure):
 
 class rf_proposal_params(ctypes.Structure):
     _fields_ = [("k_learned", ctypes.c_int), ("k_fallback", ctypes.c_int), ("kappa", ctypes.c_float),
-                ("theta", ctypes.c_float), ("r_min", ctypes.c_float * 6), ("r_max", ctypes.c_float * 6)]
+                ("theta", ctypes.c_float), ("r_min", ctypes.c_float * 6), ("r_max", ctypes.c_float * 6),
+                ("resume", ctypes.c_int)]
 
 
 class rf_learned_stats(ctypes.Structure):

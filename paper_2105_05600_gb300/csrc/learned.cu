@@ -166,22 +166,33 @@ struct LearnedState {
     float r0[6];            // proposal axis lengths
     float r_learned[6];     // r_0 of the learned run, r_1 after it
     float r_carry[6];       // r_1 carried for the plain fallback (Sec. 4)
-    float r_fb[6];          // fallback's r_0 in / r_1 out
+    float r_fb[6];          // second run's r_0 in / r_1 out
+    float c_fb[7];          // second run's centre: s*_{t-1} (restart) or the learned s* (resume)
     float pose_l[7], pose_f[7];
     float rho_prev;
-    int run_flag;
+    int run_flag;           // 0 no second run, 1 plain restart, 2 resume of the learned run
     int status;             // final status of the frame (fusion skips when != 0)
     rf_frame_stats st_l, st_f;
 };
 
-__global__ void judge_kernel(LearnedState *S, float theta)
+// Second run of a frame: a plain restart from s*_{t-1} with the carried r_1 when
+// the learned run failed or its final rho_tilde fell below theta x the previous
+// frame's; otherwise, with `resume`, a continuation from the learned run's state
+// (its s* and axis lengths) when that run used all k_learned iterations without
+// meeting a convergence criterion of Sec. 4 (stop reason k_max).
+__global__ void judge_kernel(LearnedState *S, float theta, int resume)
 {
     const rf_frame_stats &l = S->st_l;
     const float rho = final_rho(&l);
-    const bool fire = theta >= 0.f && (l.status != 0 || l.iters == 0 || rho < theta * S->rho_prev);
-    S->run_flag = fire ? 1 : 0;
+    const int last = min(l.iters, RF_MAX_ITERS) - 1;
+    const bool bad = l.status != 0 || l.iters == 0 || rho < theta * S->rho_prev;
+    const bool open = last >= 0 && l.it[last].stop == 3;
+    const int mode = theta < 0.f ? 0 : bad ? 1 : (resume && open) ? 2 : 0;
+    S->run_flag = mode;
+    for (int a = 0; a < 7; ++a)
+        S->c_fb[a] = mode == 2 ? S->pose_l[a] : S->hist[1][a];
     for (int i = 0; i < 6; ++i)
-        S->r_fb[i] = S->r_carry[i];
+        S->r_fb[i] = mode == 2 ? l.it[last].scale[i] : S->r_carry[i];
 }
 
 __global__ void select_kernel(LearnedState *S, rf_learned_stats *out_stats, float *out_pose)
@@ -193,7 +204,7 @@ __global__ void select_kernel(LearnedState *S, rf_learned_stats *out_stats, floa
     const float *p = take_f ? S->pose_f : S->pose_l;
     if (out_stats) {
         out_stats->status = take_f ? f.status : l.status;
-        out_stats->used_fallback = ran ? 1 : 0;
+        out_stats->used_fallback = ran ? S->run_flag : 0;
         out_stats->chose_fallback = take_f ? 1 : 0;
         out_stats->iters_learned = l.iters;
         out_stats->iters_fallback = ran ? f.iters : 0;
@@ -248,6 +259,7 @@ rf_status check_params(const rf_proposal_params *p)
     RF_CHECK_ARG(p->k_learned >= 1 && p->k_learned <= RF_MAX_ITERS, "k_learned outside [1, RF_MAX_ITERS]");
     RF_CHECK_ARG(p->k_fallback >= 1 && p->k_fallback <= RF_MAX_ITERS, "k_fallback outside [1, RF_MAX_ITERS]");
     RF_CHECK_ARG(p->kappa > 0.f, "kappa must be positive");
+    RF_CHECK_ARG(p->resume == 0 || p->resume == 1, "resume must be 0 or 1");
     for (int i = 0; i < 6; ++i)
         RF_CHECK_ARG(p->r_min[i] > 0.f && p->r_max[i] >= p->r_min[i], "r_min / r_max");
     return RF_OK;
@@ -297,9 +309,10 @@ static rf_status learned_enqueue(rf_learned lp, const rf_intrinsics *K, rf_learn
     st = pfo_track_frame_ex_async(lp->tr, lp->depth_cur, lp->depth_prev, K, S->hist[1], S->pose_l, &S->st_l, &o, s);
     if (st != RF_OK)
         return st;
-    judge_kernel<<<1, 1, 0, s>>>(S, lp->p.theta);
+    judge_kernel<<<1, 1, 0, s>>>(S, lp->p.theta, lp->p.resume);
     RF_CUDA(cudaGetLastError());
     memset(&o, 0, sizeof o);
+    o.init_pose_dev = S->c_fb;
     o.scale_dev = S->r_fb;
     o.run_flag_dev = &S->run_flag;
     o.k_max = lp->p.k_fallback;
@@ -326,6 +339,7 @@ void rf_proposal_default_params(rf_proposal_params *p)
     p->k_fallback = 20;
     p->kappa = 2.f;
     p->theta = 0.9f;
+    p->resume = 1;
     for (int i = 0; i < 6; ++i) {
         p->r_min[i] = i < 3 ? 2e-3f : 4e-3f;
         p->r_max[i] = i < 3 ? 0.2f : 0.4f;

@@ -282,8 +282,8 @@ def run_learned(nat, spec, traj, K, depths, net, params, use_graph=True, warmup=
     st = [nat.learned_stats_dict(rec[f]) for f in range(1, n)]
     timed = st[warmup:]
     return dict(poses=out.cpu().numpy().astype(np.float64), seconds=tm.seconds(n),
-                lookups=sum(s["lookups"] for s in timed), fallbacks=sum(s["used_fallback"] for s in st),
-                fallback_kept=sum(s["chose_fallback"] for s in st),
+                lookups=sum(s["lookups"] for s in timed), fallbacks=sum(s["used_fallback"] == 1 for s in st),
+                resumed=sum(s["used_fallback"] == 2 for s in st), fallback_kept=sum(s["chose_fallback"] for s in st),
                 iters=float(np.mean([s["iters_learned"] for s in st])),
                 failed=sum(1 for s in st if s["status"] != 0))
 
@@ -303,5 +303,6 @@ def evaluate(nat, spec, seeds, n_frames, net, params, use_graph=True, warmup=0, 
         rows.append(dict(seed=s, frames=nf, plain_s=tp, learned_s=rl["seconds"], plain_fps=nf / tp,
                          learned_fps=nf / rl["seconds"], plain_ate_cm=100 * ap, learned_ate_cm=100 * al,
                          plain_lookups=lkp, learned_lookups=rl["lookups"], fallbacks=rl["fallbacks"],
+                         resumed=rl["resumed"],
                          fallback_kept=rl["fallback_kept"], learned_iters=rl["iters"], failed_frames=rl["failed"]))
     return rows

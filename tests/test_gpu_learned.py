@@ -174,7 +174,8 @@ def test_fallback_rule_and_graph_replay(nat, tiny):
         net = nat.MLP(16)
         net.set_params(zero_network_params(np.log(0.2)))
         # theta = 2: every frame after the first (rho_prev > 0) runs the fallback
-        lp = nat.Learned(tr, gv, net, nat.proposal_params(k_learned=2, theta=2.0), cfg["width"], cfg["height"])
+        lp = nat.Learned(tr, gv, net, nat.proposal_params(k_learned=2, theta=2.0, resume=0), cfg["width"],
+                         cfg["height"])
         lp.start(tiny["depths"][0], K, pose_f32(traj[0]))
         sb = nat.new_learned_stats_buffer()
         poses, stats = [], []
@@ -194,3 +195,56 @@ def test_fallback_rule_and_graph_replay(nat, tiny):
     # graph replay gives the same frames bit for bit
     np.testing.assert_array_equal(runs[True][0], poses)
     assert [s["chose_fallback"] for s in runs[True][1]] == [s["chose_fallback"] for s in stats]
+
+
+def test_resume_continues_the_learned_run(nat, tiny):
+    # theta = 0 never judges the proposal poor, so a learned run that used its one
+    # iteration without converging is resumed from its own s* and axis lengths:
+    # the step must equal the two explicit extended-frame calls it stands for.
+    import torch
+
+    cfg, K, traj = tiny["cfg"], tiny["K"], tiny["traj"]
+    n, k_fb = cfg["n_particles"], 20
+    prev = pose_f32(traj[0])
+    d0, d1 = (torch.from_numpy(tiny["depths"][f]).cuda() for f in (0, 1))
+    params = nat.make_params(k_max=20, stride=cfg["stride"])
+
+    gv = gpu_volume(nat, tiny)
+    tr = nat.Tracker(gv, nat.pst_create(n, seed=1), params, cfg["width"], cfg["height"])
+    net = nat.MLP(16)
+    net.set_params(zero_network_params(np.log(0.3)))
+    lp = nat.Learned(tr, gv, net, nat.proposal_params(k_learned=1, k_fallback=k_fb, theta=0.0, resume=1),
+                     cfg["width"], cfg["height"])
+    lp.start(tiny["depths"][0], K, prev)
+    sb = nat.new_learned_stats_buffer()
+    pose, status = lp.step(tiny["depths"][1], K, stats_dev=sb)
+    s = nat.learned_stats_dict(sb)
+    assert status == 0 and s["iters_learned"] == 1
+
+    # the same frame by hand: frame 0 fused at prev, the learned run, then the resumed run
+    gv2 = gpu_volume(nat, tiny)
+    nat.tsdf_integrate(gv2, d0, K, prev)
+    tr2 = nat.Tracker(gv2, nat.pst_create(n, seed=1), params, cfg["width"], cfg["height"])
+    prev_dev = torch.tensor(prev, dtype=torch.float32, device="cuda")
+    c0 = torch.tensor(s["init_pose"], dtype=torch.float32, device="cuda")
+    r = torch.tensor(s["r0"], dtype=torch.float32, device="cuda")
+    pose_l = torch.zeros(7, dtype=torch.float32, device="cuda")
+    st_l = nat.new_stats_buffer()
+    nat.pfo_track_frame_ex_async(tr2, d1, d0, K, prev_dev, pose_l, st_l, init_pose_dev=c0, scale_dev=r, k_max=1)
+    sl = nat.stats_dict(nat.stats_from_device(st_l))
+    assert sl["iters"] == 1
+    if sl["it"][0]["stop"] != 3:  # converged (small step) in one iteration: nothing to resume
+        assert s["used_fallback"] == 0
+        return
+    assert s["used_fallback"] == 2
+    r1 = torch.tensor(sl["it"][0]["scale"], dtype=torch.float32, device="cuda")
+    pose_f = torch.zeros(7, dtype=torch.float32, device="cuda")
+    st_f = nat.new_stats_buffer()
+    nat.pfo_track_frame_ex_async(tr2, d1, d0, K, prev_dev, pose_f, st_f, init_pose_dev=pose_l.clone(),
+                                 scale_dev=r1, k_max=k_fb)
+    sf = nat.stats_dict(nat.stats_from_device(st_f))
+    assert s["iters_fallback"] == sf["iters"] >= 1
+    assert s["rho_fallback"] == sf["it"][-1]["rho_tilde"] and s["rho_learned"] == sl["it"][-1]["rho_tilde"]
+    want = (pose_f if s["rho_fallback"] > s["rho_learned"] else pose_l).cpu().numpy().astype(np.float64)
+    assert s["chose_fallback"] == int(s["rho_fallback"] > s["rho_learned"])
+    np.testing.assert_array_equal(np.asarray(pose, dtype=np.float32), want.astype(np.float32))

@@ -104,3 +104,23 @@ def test_template_must_start_at_origin(oracle):
                       np.array([1, 0, 0, 0, 0, 0, 0.0]), np.array([1, 0, 0, 0, 0, 0, 0.0]), np.ones(6), omega,
                       _params(oracle))
     assert res["status"] == -1
+
+
+def test_centre_particle_is_never_in_the_aps(oracle):
+    # The APS holds particles better than s*_{k-1} (Sec. 3.3); particle 0 is s*_{k-1}
+    # itself.  Late in this run the carried Eq. wafit threshold lies below the centre's
+    # own fitness while every other particle is below it: the centre is the arg max and
+    # the second-best fitness is <= rho_ref < rho_max.  Such an iteration must report
+    # an empty APS, no step, and must not end on the small-step rule.
+    scene, v = _scene_volume(oracle)
+    K = synth.intrinsics(20, 15)
+    eye = np.array([0.72, 0.70, 0.68])
+    T = np.concatenate([synth.look_at_quat(eye, [1.5, 1.45, 1.5]), eye])
+    depth = synth.render_depth(scene, T, K)
+    pts = oracle.unproject(depth, K, 1)
+    c0 = oracle.compose_offset(T, [0.004, -0.006, 0.005, 0.01, -0.01, 0.008])
+    res = v.pfo_frame(pts, depth, K, c0, c0, np.full(6, 0.1), oracle.pst_uniform(16, seed=4), _params(oracle))
+    only_centre = [row for row in res["trace"] if row[6] == 0 and row[29] <= row[3] < row[5]]
+    assert only_centre  # the case occurs in this run
+    for row in only_centre:
+        assert row[2] == 0 and np.all(row[20:26] == 0.0) and row[28] != 2

@@ -237,26 +237,38 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def _reduce(x, world, op):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(x, world):
+    import torch.distributed as dist
+
+    return _reduce(x, world, dist.ReduceOp.MAX)
 
 
 def sum_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, dist.ReduceOp.SUM)
+
+
+def job_rate(units, seconds, world):
+    """Whole-job throughput: the units of all ranks over the slowest rank's time."""
+    return sum_over_ranks(float(units), world) / max_over_ranks(float(seconds), world)
+
+
+def rank_seeds(seeds, rank, stride=1000):
+    """Sequence seeds of one rank: every rank runs its own, disjoint sequences."""
+    return [int(s) + stride * rank for s in seeds]
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -582,8 +594,8 @@ def run_learned_bench(args):
     n_test = args.test_seqs or len(spec["test_seeds"])
     frames = args.frames or spec["frames"]
     W = max(3, args.warmup)
-    seeds_tr = [s + 1000 * rank for s in spec["train_seeds"][:n_train]]
-    seeds_te = [s + 1000 * rank for s in spec["test_seeds"][:n_test]]
+    seeds_tr = rank_seeds(spec["train_seeds"][:n_train], rank)
+    seeds_te = rank_seeds(spec["test_seeds"][:n_test], rank)
     ds = learned.generate_dataset(nat, spec, seeds_tr, train_frames, substeps=spec["label_substeps"])
     n_val = max(1, n_train // 8)
     seq = ds["seq"]
@@ -780,7 +792,7 @@ def run_ablation_bench(args):
     from paper_2105_05600_gb300 import _native as nat
 
     spec = dict(synth.CONFIGS["learned"], speed=args.speed or 1.5, ang_speed=args.ang_speed or 0.75)  # FastCaMo-Synth means
-    seeds = [s + 1000 * rank for s in spec["test_seeds"][:args.test_seqs or 3]]
+    seeds = rank_seeds(spec["test_seeds"][:args.test_seqs or 3], rank)
     frames = args.frames or 200
     W = max(3, args.warmup)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")

@@ -114,15 +114,57 @@ template <> struct Enc<RF_I16> {
     }
 };
 
+// Bricks handled by one CTA of the fusion kernels (one brick per loop step).
+constexpr int FUSE_BRICKS_PER_CTA = 8;
+static_assert(FUSE_BRICKS_PER_CTA == 8, "the dirty-flag scan of pack_cells_kernel maps 8 bricks x 8 neighbours to warp 0");
+
+// Conservative test of whether brick (bx, by, bz) can hold a voxel that the
+// per-voxel fusion test accepts: the sphere around the brick's voxel centres
+// (radius 3.5 sqrt(3) voxels, plus a margin far above FP32 rounding) must meet
+// every half-space whose intersection contains the accepted voxels -- in front
+// of the camera (z > 0), no deeper than z_max + trunc (sdf = D - z >= -trunc
+// with D <= z_max), and re-projecting into the image (the rounded pixel lies in
+// [0, W) x [0, H), i.e. -1/2 <= u < W - 1/2 and likewise v).  A brick that
+// fails any test has no voxel to update, so skipping it changes nothing.
+__device__ __forceinline__ bool brick_may_update(const VolumeDesc &V, int bx, int by, int bz, const float R[9],
+                                                 const float t[3], const Intr &K)
+{
+    const float h = V.voxel;
+    const float wx = V.origin[0] + h * (float)(bx * BRICK + BRICK / 2) - t[0];
+    const float wy = V.origin[1] + h * (float)(by * BRICK + BRICK / 2) - t[1];
+    const float wz = V.origin[2] + h * (float)(bz * BRICK + BRICK / 2) - t[2];
+    const float px = R[0] * wx + R[3] * wy + R[6] * wz;
+    const float py = R[1] * wx + R[4] * wy + R[7] * wz;
+    const float pz = R[2] * wx + R[5] * wy + R[8] * wz;
+    const float rad = h * (0.5f * (float)(BRICK - 1) * 1.7320508f + 0.05f);
+    if (pz + rad <= 0.f || pz - rad > K.z_max + V.trunc)
+        return false;
+    const float l0 = K.cx + 0.5f, r0 = (float)K.width - 0.5f - K.cx;
+    const float t0 = K.cy + 0.5f, b0 = (float)K.height - 0.5f - K.cy;
+    if (K.fx * px + l0 * pz < -rad * sqrtf(K.fx * K.fx + l0 * l0))
+        return false;
+    if (r0 * pz - K.fx * px < -rad * sqrtf(K.fx * K.fx + r0 * r0))
+        return false;
+    if (K.fy * py + t0 * pz < -rad * sqrtf(K.fy * K.fy + t0 * t0))
+        return false;
+    if (b0 * pz - K.fy * py < -rad * sqrtf(K.fy * K.fy + b0 * b0))
+        return false;
+    return true;
+}
+
 // Projective TSDF fusion (Sec. 3 overview; Curless & Levoy 1996, KinectFusion
-// 2011).  One CTA per 8x8x8 brick, one thread per voxel, so value and weight
-// accesses are contiguous 1 KiB (or 2 KiB) runs.  HBM-bound: 2+2 B of value
-// (4+4 for float) and 1+1 B of weight per updated voxel plus the depth reads.
-// The pose comes by value, or from device memory (pose_dev != NULL, written by
-// the tracker earlier on the stream); a non-zero *status_dev skips the update.
+// 2011).  Each CTA walks FUSE_BRICKS_PER_CTA consecutive 8x8x8 bricks with one
+// thread per voxel, so value and weight accesses are contiguous 1 KiB (or 2 KiB)
+// runs; thread 0 first tests the brick against the view frustum and the depth
+// range (brick_may_update) and the CTA skips bricks that cannot change.  Per
+// updated voxel 2+2 B of value (4+4 for float) and 1+1 B of weight plus the
+// depth reads.  The pose comes by value, or from device memory (pose_dev !=
+// NULL, written by the tracker earlier on the stream); a non-zero *status_dev
+// skips the update.
 template <int DT>
 __global__ void __launch_bounds__(512) integrate_kernel(VolumeDesc V, const float *__restrict__ depth, Intr K, Pose T,
-                                                        const float *pose_dev, const int *status_dev, int w_max)
+                                                        const float *pose_dev, const int *status_dev, int w_max,
+                                                        int nbricks)
 {
     using S = typename Storage<DT>::T;
     if (status_dev && *((volatile const int *)status_dev) != 0)
@@ -133,75 +175,78 @@ __global__ void __launch_bounds__(512) integrate_kernel(VolumeDesc V, const floa
         for (int a = 0; a < 3; ++a)
             T.t[a] = pose_dev[4 + a];
     }
-    const int b = blockIdx.x;
-    const int bx = b % V.nb[0], by = (b / V.nb[0]) % V.nb[1], bz = b / (V.nb[0] * V.nb[1]);
+    float R[9];
+    quat_rot(T.q, R);
+    // lane j of warp 0 tests brick j of this CTA; one barrier publishes the mask
+    __shared__ unsigned s_visible;
     const int l = threadIdx.x;
-    const int x = bx * BRICK + (l & 7), y = by * BRICK + ((l >> 3) & 7), z = bz * BRICK + (l >> 6);
-    bool updated = false;
-    do {
-        float R[9];
-        quat_rot(T.q, R);
-        const float pwx = V.origin[0] + V.voxel * ((float)x + 0.5f) - T.t[0];
-        const float pwy = V.origin[1] + V.voxel * ((float)y + 0.5f) - T.t[1];
-        const float pwz = V.origin[2] + V.voxel * ((float)z + 0.5f) - T.t[2];
-        // camera frame: R^T (p - t)
-        const float cx = R[0] * pwx + R[3] * pwy + R[6] * pwz;
-        const float cy = R[1] * pwx + R[4] * pwy + R[7] * pwz;
-        const float cz = R[2] * pwx + R[5] * pwy + R[8] * pwz;
-        if (!(cz > 0.f))
-            break;
-        const float u = floorf(K.fx * cx / cz + K.cx + 0.5f);
-        const float v = floorf(K.fy * cy / cz + K.cy + 0.5f);
-        if (!(u >= 0.f && u < (float)K.width && v >= 0.f && v < (float)K.height))
-            break;
-        const float D = __ldg(&depth[(size_t)v * K.width + (size_t)u]);
-        if (!depth_valid(D, K))
-            break;
-        const float sdf = D - cz;
-        if (sdf < -V.trunc)
-            break;
-        const float f = fminf(1.f, sdf / V.trunc);
-        const size_t idx = (size_t)b * BRICK_VOX + l;
-        S *vals = reinterpret_cast<S *>(V.values);
-        const S old = vals[idx];
-        int w_old = V.weights[idx];
-        float F_old = 0.f;
-        if (Enc<DT>::unobserved(old))
-            w_old = 0;
-        else
-            F_old = Enc<DT>::dec(old);
-        const float F_new = ((float)w_old * F_old + f) / (float)(w_old + 1);
-        vals[idx] = Enc<DT>::enc(F_new);
-        V.weights[idx] = (uint8_t)min(w_old + 1, w_max);
-        updated = true;
-    } while (false);
-    // mark the brick so that its packed cells (and those of the cells reaching
-    // into it from the lower neighbours) are rebuilt
-    if (__syncthreads_or(updated) && l == 0)
-        V.dirty[b] = 1;
+    if (l < 32) {
+        const int b = blockIdx.x * FUSE_BRICKS_PER_CTA + l;
+        bool vis = false;
+        if (l < FUSE_BRICKS_PER_CTA && b < nbricks)
+            vis = brick_may_update(V, b % V.nb[0], (b / V.nb[0]) % V.nb[1], b / (V.nb[0] * V.nb[1]), R, T.t, K);
+        const unsigned m = __ballot_sync(0xffffffffu, vis);
+        if (l == 0)
+            s_visible = m;
+    }
+    __syncthreads();
+    const unsigned visible = s_visible;
+    for (int j = 0; j < FUSE_BRICKS_PER_CTA; ++j) {
+        if (!((visible >> j) & 1u))
+            continue;  // uniform across the CTA (also every brick past the end)
+        const int b = blockIdx.x * FUSE_BRICKS_PER_CTA + j;
+        const int bx = b % V.nb[0], by = (b / V.nb[0]) % V.nb[1], bz = b / (V.nb[0] * V.nb[1]);
+        const int x = bx * BRICK + (l & 7), y = by * BRICK + ((l >> 3) & 7), z = bz * BRICK + (l >> 6);
+        bool updated = false;
+        do {
+            const float pwx = V.origin[0] + V.voxel * ((float)x + 0.5f) - T.t[0];
+            const float pwy = V.origin[1] + V.voxel * ((float)y + 0.5f) - T.t[1];
+            const float pwz = V.origin[2] + V.voxel * ((float)z + 0.5f) - T.t[2];
+            // camera frame: R^T (p - t)
+            const float cx = R[0] * pwx + R[3] * pwy + R[6] * pwz;
+            const float cy = R[1] * pwx + R[4] * pwy + R[7] * pwz;
+            const float cz = R[2] * pwx + R[5] * pwy + R[8] * pwz;
+            if (!(cz > 0.f))
+                break;
+            const float u = floorf(K.fx * cx / cz + K.cx + 0.5f);
+            const float v = floorf(K.fy * cy / cz + K.cy + 0.5f);
+            if (!(u >= 0.f && u < (float)K.width && v >= 0.f && v < (float)K.height))
+                break;
+            const float D = __ldg(&depth[(size_t)v * K.width + (size_t)u]);
+            if (!depth_valid(D, K))
+                break;
+            const float sdf = D - cz;
+            if (sdf < -V.trunc)
+                break;
+            const float f = fminf(1.f, sdf / V.trunc);
+            const size_t idx = (size_t)b * BRICK_VOX + l;
+            S *vals = reinterpret_cast<S *>(V.values);
+            const S old = vals[idx];
+            int w_old = V.weights[idx];
+            float F_old = 0.f;
+            if (Enc<DT>::unobserved(old))
+                w_old = 0;
+            else
+                F_old = Enc<DT>::dec(old);
+            const float F_new = ((float)w_old * F_old + f) / (float)(w_old + 1);
+            vals[idx] = Enc<DT>::enc(F_new);
+            V.weights[idx] = (uint8_t)min(w_old + 1, w_max);
+            updated = true;
+        } while (false);
+        // mark the brick so that its packed cells (and those of the cells reaching
+        // into it from the lower neighbours) are rebuilt
+        if (__syncthreads_or(updated) && l == 0)
+            V.dirty[b] = 1;
+    }
 }
 
-// Packed trilinear cells of the bricks whose values may have changed: cell i
-// reads voxels i + {0,1}^3, so brick B needs repacking when any of the bricks
-// B + {0,1}^3 is dirty.  One CTA per brick, one thread per cell.  Cells on the
-// upper faces of the volume are never sampled; they copy the nearest voxels.
+// Packed trilinear cells of one brick (one thread per cell) and its class.
+// Cell i reads voxels i + {0,1}^3; cells on the upper faces of the volume are
+// never sampled and copy the nearest voxels.
 template <int DT>
-__global__ void __launch_bounds__(512) pack_cells_kernel(VolumeDesc V, int all)
+__device__ __forceinline__ void pack_brick(const VolumeDesc &V, int b, int bx, int by, int bz, int l)
 {
     using S = typename Storage<DT>::T;
-    const int b = blockIdx.x;
-    const int bx = b % V.nb[0], by = (b / V.nb[0]) % V.nb[1], bz = b / (V.nb[0] * V.nb[1]);
-    if (!all) {
-        bool need = false;
-        for (int c = 0; c < 8; ++c) {
-            const int nx = bx + (c & 1), ny = by + ((c >> 1) & 1), nz = bz + (c >> 2);
-            if (nx < V.nb[0] && ny < V.nb[1] && nz < V.nb[2])
-                need |= V.dirty[nx + V.nb[0] * (ny + V.nb[1] * nz)] != 0;
-        }
-        if (!need)
-            return;
-    }
-    const int l = threadIdx.x;
     const int x = bx * BRICK + (l & 7), y = by * BRICK + ((l >> 3) & 7), z = bz * BRICK + (l >> 6);
     const S *vals = reinterpret_cast<const S *>(V.values);
     S c[8];
@@ -246,20 +291,63 @@ __global__ void __launch_bounds__(512) pack_cells_kernel(VolumeDesc V, int all)
         V.brick_class[b] = every_free ? CELLS_FREE : (every_invalid ? CELLS_INVALID : CELLS_MIXED);
 }
 
+
+// Packed cells of the bricks whose values may have changed: brick B needs
+// repacking when any of the bricks B + {0,1}^3 is dirty (or `all`).  Each CTA
+// walks FUSE_BRICKS_PER_CTA consecutive bricks; thread 0 reads the dirty flags
+// and the CTA skips bricks that need nothing.
+template <int DT>
+__global__ void __launch_bounds__(512) pack_cells_kernel(VolumeDesc V, int all, int nbricks)
+{
+    // warp 0 reads the 8 x 8 dirty flags of this CTA's bricks in parallel (lane
+    // i: brick i / 8 and i / 8 + 4, neighbour i % 8); one barrier publishes the mask
+    __shared__ unsigned s_need;
+    const int l = threadIdx.x;
+    if (l < 32) {
+        unsigned bits = 0u;
+        for (int half = 0; half < 2; ++half) {
+            const int j = (l >> 3) + 4 * half, c = l & 7;
+            const int b = blockIdx.x * FUSE_BRICKS_PER_CTA + j;
+            bool d = false;
+            if (b < nbricks) {
+                const int bx = b % V.nb[0], by = (b / V.nb[0]) % V.nb[1], bz = b / (V.nb[0] * V.nb[1]);
+                const int nx = bx + (c & 1), ny = by + ((c >> 1) & 1), nz = bz + (c >> 2);
+                d = all != 0 || (nx < V.nb[0] && ny < V.nb[1] && nz < V.nb[2] &&
+                                 V.dirty[nx + V.nb[0] * (ny + V.nb[1] * nz)] != 0);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, d);  // bit 8 q + c: brick q (+ 4 half)
+            for (int q = 0; q < 4; ++q)
+                if ((m >> (8 * q)) & 0xffu)
+                    bits |= 1u << (q + 4 * half);
+        }
+        if (l == 0)
+            s_need = bits;
+    }
+    __syncthreads();
+    const unsigned need = s_need;
+    for (int j = 0; j < FUSE_BRICKS_PER_CTA; ++j) {
+        if (!((need >> j) & 1u))
+            continue;  // uniform across the CTA (also every brick past the end)
+        const int b = blockIdx.x * FUSE_BRICKS_PER_CTA + j;
+        pack_brick<DT>(V, b, b % V.nb[0], (b / V.nb[0]) % V.nb[1], b / (V.nb[0] * V.nb[1]), l);
+    }
+}
+
 // Rebuild the packed cells after the values changed (all = every brick, else
 // the dirty ones), then clear the dirty flags.  Stream-ordered, capturable.
 rf_status pack_cells(const VolumeDesc &V, int all, cudaStream_t s)
 {
     const int nbricks = V.nb[0] * V.nb[1] * V.nb[2];
+    const int grid = (nbricks + FUSE_BRICKS_PER_CTA - 1) / FUSE_BRICKS_PER_CTA;
     switch (V.dtype) {
     case RF_F32:
-        pack_cells_kernel<RF_F32><<<nbricks, 512, 0, s>>>(V, all);
+        pack_cells_kernel<RF_F32><<<grid, 512, 0, s>>>(V, all, nbricks);
         break;
     case RF_F16:
-        pack_cells_kernel<RF_F16><<<nbricks, 512, 0, s>>>(V, all);
+        pack_cells_kernel<RF_F16><<<grid, 512, 0, s>>>(V, all, nbricks);
         break;
     default:
-        pack_cells_kernel<RF_I16><<<nbricks, 512, 0, s>>>(V, all);
+        pack_cells_kernel<RF_I16><<<grid, 512, 0, s>>>(V, all, nbricks);
         break;
     }
     RF_CUDA(cudaGetLastError());
@@ -271,15 +359,16 @@ static rf_status integrate_any(const VolumeDesc &V, const float *depth, const In
                                const float *pose_dev, const int *status_dev, cudaStream_t s)
 {
     const int nbricks = V.nb[0] * V.nb[1] * V.nb[2];
+    const int grid = (nbricks + FUSE_BRICKS_PER_CTA - 1) / FUSE_BRICKS_PER_CTA;
     switch (V.dtype) {
     case RF_F32:
-        integrate_kernel<RF_F32><<<nbricks, 512, 0, s>>>(V, depth, K, T, pose_dev, status_dev, 255);
+        integrate_kernel<RF_F32><<<grid, 512, 0, s>>>(V, depth, K, T, pose_dev, status_dev, 255, nbricks);
         break;
     case RF_F16:
-        integrate_kernel<RF_F16><<<nbricks, 512, 0, s>>>(V, depth, K, T, pose_dev, status_dev, 255);
+        integrate_kernel<RF_F16><<<grid, 512, 0, s>>>(V, depth, K, T, pose_dev, status_dev, 255, nbricks);
         break;
     default:
-        integrate_kernel<RF_I16><<<nbricks, 512, 0, s>>>(V, depth, K, T, pose_dev, status_dev, 255);
+        integrate_kernel<RF_I16><<<grid, 512, 0, s>>>(V, depth, K, T, pose_dev, status_dev, 255, nbricks);
         break;
     }
     RF_CUDA(cudaGetLastError());

@@ -91,20 +91,26 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.path = None
+        self.fh = None
 
     def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        self.fh = os.fdopen(fd, "w")
         try:
-            self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
+        except OSError:
             self.proc = None
         return self
 
     def stop(self):
         if self.proc is None:
+            if self.fh is not None:
+                self.fh.close()
+                os.unlink(self.path)
+                self.fh = None
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:

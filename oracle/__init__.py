@@ -13,7 +13,9 @@ Zhang et al., ACM TOG 40(4) 2021):
     overlap ....................... Sec. 4 Eq. validness
     tsdf_sample / fitness ......... Sec. 3.1 Eq. likelihood, Sec. 4 Eq. normallh
     pst_update .................... Sec. 3.3 Eq. ebs, rsdir, rsinter, momentum; Eq. wafit
-    pfo_frame ..................... Algorithm 1 + Sec. 4 initialisation / stop rules
+    pfo_step ...................... one iteration of Algorithm 1 (state in, state out)
+    pfo_frame / pfo_frame_sched ... Algorithm 1 + Sec. 4 initialisation / stop rules / corner cases
+    fitness_particles ............. Eq. normallh for a range of template particles
     tsdf_integrate ................ Sec. 3 overview (Curless-Levoy volumetric fusion)
     pst_uniform / philox .......... Sec. 4 "PST pre-sampling" (uniform unit 6D ball)
     ate / te ...................... Sec. 5.1 ATE, Eq. te
@@ -33,8 +35,16 @@ _SO = os.path.join(_BUILD, "librf_oracle.so")
 _SRC = os.path.join(_HERE, "rf_oracle.c")
 
 OVERLAP, NORMALIZE, COMPENSATED, NEAREST, RHO_REF_CENTER, L1, RIGHT_MULT, CELL_MARGIN = 1, 2, 4, 8, 16, 32, 64, 128
+APS_WITH_CENTRE = 256
 DEFAULT_FLAGS = OVERLAP | NORMALIZE | COMPENSATED | CELL_MARGIN
 TRACE_STRIDE = 40
+STATE_LEN = 16
+TIE_PX, TIE_RHO = 1e-3, 1e-5  # decision margins the trace counts (columns 35, 36)
+# trace columns (see rf_oracle.c)
+T_K, T_NO, T_NAPS, T_RHO_REF, T_RHO_TILDE, T_RHO_MAX, T_ARGMAX = 0, 1, 2, 3, 4, 5, 6
+T_POSE, T_SCALE, T_DBAR = slice(7, 14), slice(14, 20), slice(20, 26)
+T_MIN_GAP, T_MIN_MARGIN, T_STOP, T_RHO_2ND, T_LEVEL, T_NL = 26, 27, 28, 29, 30, 31
+T_CORNER, T_VALID, T_EMPTY_RUN, T_FRAGILE_PX, T_TIES, T_SENS, T_STEP, T_SENS2 = 32, 33, 34, 35, 36, 37, 38, 39
 QMODE = {"f64": 0, "f32": 1, "f16": 2, "i16": 3}
 
 _lock = threading.Lock()
@@ -46,7 +56,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-pthread",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
@@ -78,6 +88,14 @@ def _load():
             lib.or_pfo_frame.argtypes = [D, I, d, D, D, i, F, i, i, d, d, d, d, d, d, D, D, D, F, i,
                                          d, d, d, d, i, i, D, D, D, I]
             lib.or_pfo_frame.restype = i
+            lib.or_pfo_frame_mt.argtypes = [D, I, d, D, D, i, F, i, i, d, d, d, d, d, d, D, D, D, F, i,
+                                            d, d, d, d, i, i, i, D, D, D, I]
+            lib.or_pfo_frame_mt.restype = i
+            lib.or_pfo_step.argtypes = [D, I, d, D, D, i, i, F, i, i, d, d, d, d, d, d, D, F, i, d, d, d, d, i, i,
+                                        i, i, D, D]
+            lib.or_pfo_step.restype = i
+            lib.or_fitness_particles.argtypes = [D, I, d, D, D, I, i, D, D, F, i, i, i, d, i, i, D, I, D]
+            lib.or_tsdf_integrate_mt.argtypes = [D, I, I, d, D, d, i, i, F, i, i, d, d, d, d, d, d, D, i]
             lib.or_quantize.argtypes = [d, i]
             lib.or_quantize.restype = d
             lib.or_tsdf_integrate.argtypes = [D, I, I, d, D, d, i, i, F, i, i, d, d, d, d, d, d, D]
@@ -93,6 +111,9 @@ def _load():
             lib.or_pfo_frame_sched.argtypes = [D, I, d, D, i, I, ctypes.POINTER(D), I, F, i, i, d, d, d, d, d, d, D,
                                                D, D, F, i, d, d, d, d, i, i, D, D, D, I]
             lib.or_pfo_frame_sched.restype = i
+            lib.or_pfo_frame_sched_mt.argtypes = [D, I, d, D, i, I, ctypes.POINTER(D), I, F, i, i, d, d, d, d, d, d,
+                                                  D, D, D, F, i, d, d, d, d, i, i, i, D, D, D, I]
+            lib.or_pfo_frame_sched_mt.restype = i
             lib.or_tsdf_integrate_ambiguity.argtypes = [I, d, D, d, F, i, i, d, d, d, d, d, d, D, d, I]
             _lib = lib
     return _lib
@@ -203,18 +224,22 @@ class Volume:
         d = self.dims
         return self.F.reshape(d[2], d[1], d[0])
 
-    def integrate(self, depth, K, pose):
-        """Volumetric fusion of one depth frame at pose (Sec. 3 overview)."""
+    def integrate(self, depth, K, pose, threads=1):
+        """Volumetric fusion of one depth frame at pose (Sec. 3 overview); threads
+        splits the voxel slices (same result for any count)."""
         lib = _load()
         depth, pdp = _f(depth)
         H, W = depth.shape
         pose, pp = _d(pose)
         _, pdim = _i(self.dims)
         _, por = _d(self.origin)
-        lib.or_tsdf_integrate(self.F.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                              self.W.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), pdim, self.voxel, por,
-                              self.trunc, self.w_max, self.qmode, pdp, W, H, K["fx"], K["fy"], K["cx"], K["cy"],
-                              K["z_min"], K["z_max"], pp)
+        args = (self.F.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                self.W.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), pdim, self.voxel, por, self.trunc, self.w_max,
+                self.qmode, pdp, W, H, K["fx"], K["fy"], K["cx"], K["cy"], K["z_min"], K["z_max"], pp)
+        if threads == 1:
+            lib.or_tsdf_integrate(*args)
+        else:
+            lib.or_tsdf_integrate_mt(*args, int(threads))
 
     def sample(self, p, flags=0):
         lib = _load()
@@ -284,10 +309,10 @@ class Volume:
                                  pin, pts.shape[0], pc, ph, int(steps), float(tau), int(flags), pb)
         return rho, best
 
-    def pfo_frame_sched(self, level_pts, level_n, prev_depth, K, pose_prev, c0, r0, omega, params):
+    def pfo_frame_sched(self, level_pts, level_n, prev_depth, K, pose_prev, c0, r0, omega, params, threads=1):
         """Algorithm 1 with multi-resolution alternation (Sec. 4): level l uses the
         first level_n[l] template rows and the point set level_pts[l].  Same
-        return value as pfo_frame; trace rows add the level (col 30) and N_l (31)."""
+        return value as pfo_frame."""
         lib = _load()
         L = len(level_pts)
         arrs = [np.ascontiguousarray(p, dtype=np.float64) for p in level_pts]
@@ -308,16 +333,20 @@ class Volume:
         r1, pr1 = _d(np.zeros(6))
         trace, ptr = _d(np.zeros((k_max, TRACE_STRIDE)))
         iters = ctypes.c_int(0)
-        st = lib.or_pfo_frame_sched(self.F.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pdim, self.voxel, por, L,
-                                    pln, ptrs, plm, pdp, W, H, K["fx"], K["fy"], K["cx"], K["cy"], K["z_min"],
-                                    K["z_max"], ppv, pc0, pr0, pom, N, float(params["tau"]), float(params["beta"]),
-                                    float(params["eps"]), float(params["stop_eps"]), k_max, int(params["flags"]), ppo,
-                                    pr1, ptr, ctypes.byref(iters))
+        args = [self.F.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pdim, self.voxel, por, L, pln, ptrs, plm, pdp,
+                W, H, K["fx"], K["fy"], K["cx"], K["cy"], K["z_min"], K["z_max"], ppv, pc0, pr0, pom, N,
+                float(params["tau"]), float(params["beta"]), float(params["eps"]), float(params["stop_eps"]), k_max,
+                int(params["flags"])]
+        if threads == 1:
+            st = lib.or_pfo_frame_sched(*args, ppo, pr1, ptr, ctypes.byref(iters))
+        else:
+            st = lib.or_pfo_frame_sched_mt(*args, int(threads), ppo, pr1, ptr, ctypes.byref(iters))
         return dict(status=st, pose=pose, r1=r1, iters=iters.value, trace=trace[:iters.value])
 
-    def pfo_frame(self, pts, prev_depth, K, pose_prev, c0, r0, omega, params):
+    def pfo_frame(self, pts, prev_depth, K, pose_prev, c0, r0, omega, params, threads=1):
         """Algorithm 1 for one frame.  params: dict(tau, beta, eps, stop_eps, k_max, flags).
-        Returns dict(status, pose, r1, iters, trace[iters, TRACE_STRIDE])."""
+        Returns dict(status, pose, r1, iters, trace[iters, TRACE_STRIDE]); threads
+        splits the per-particle fitness loop (same result for any count)."""
         lib = _load()
         pts, pp = _d(pts)
         prev_depth, pdp = _f(prev_depth)
@@ -334,12 +363,65 @@ class Volume:
         r1, pr1 = _d(np.zeros(6))
         trace, ptr = _d(np.zeros((k_max, TRACE_STRIDE)))
         iters = ctypes.c_int(0)
-        st = lib.or_pfo_frame(self.F.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pdim, self.voxel, por, pp,
-                              pts.shape[0], pdp, W, H, K["fx"], K["fy"], K["cx"], K["cy"], K["z_min"], K["z_max"],
-                              ppv, pc0, pr0, pom, N, float(params["tau"]), float(params["beta"]),
-                              float(params["eps"]), float(params["stop_eps"]), k_max, int(params["flags"]), ppo,
-                              pr1, ptr, ctypes.byref(iters))
+        args = [self.F.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pdim, self.voxel, por, pp, pts.shape[0], pdp,
+                W, H, K["fx"], K["fy"], K["cx"], K["cy"], K["z_min"], K["z_max"], ppv, pc0, pr0, pom, N,
+                float(params["tau"]), float(params["beta"]), float(params["eps"]), float(params["stop_eps"]), k_max,
+                int(params["flags"])]
+        if threads == 1:
+            st = lib.or_pfo_frame(*args, ppo, pr1, ptr, ctypes.byref(iters))
+        else:
+            st = lib.or_pfo_frame_mt(*args, int(threads), ppo, pr1, ptr, ctypes.byref(iters))
         return dict(status=st, pose=pose, r1=r1, iters=iters.value, trace=trace[:iters.value])
+
+    def pfo_step(self, pts, n_level, prev_depth, K, pose_prev, omega, params, state, centre_ref=False, threads=1):
+        """One iteration of Algorithm 1 (see or_pfo_step) on the first n_level
+        template particles.  state = dict(c, r, rho_carry, empty_run, k) is the
+        state before the iteration.  Returns (stop code, new state dict, trace row)."""
+        lib = _load()
+        pts, pp = _d(pts)
+        prev_depth, pdp = _f(prev_depth)
+        H, W = prev_depth.shape
+        pose_prev, ppv = _d(pose_prev)
+        omega, pom = _f(omega)
+        N = omega.shape[1]
+        _, pdim = _i(self.dims)
+        _, por = _d(self.origin)
+        st = np.zeros(STATE_LEN)
+        st[0:7] = state["c"]
+        st[7:13] = state["r"]
+        st[13] = state.get("rho_carry", 0.0)
+        st[14] = state.get("empty_run", 0)
+        st[15] = state["k"]
+        st, pst = _d(st)
+        row, prow = _d(np.zeros(TRACE_STRIDE))
+        stop = lib.or_pfo_step(self.F.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pdim, self.voxel, por, pp,
+                               pts.shape[0], int(n_level), pdp, W, H, K["fx"], K["fy"], K["cx"], K["cy"], K["z_min"],
+                               K["z_max"], ppv, pom, N, float(params["tau"]), float(params["beta"]),
+                               float(params["eps"]), float(params["stop_eps"]), int(params["k_max"]),
+                               int(params["flags"]), int(bool(centre_ref)), int(threads), pst, prow)
+        new = dict(c=st[0:7].copy(), r=st[7:13].copy(), rho_carry=float(st[13]), empty_run=int(st[14]),
+                   k=int(st[15]))
+        return stop, new, row
+
+    def fitness_particles(self, pts, mask, c, r, omega, i_begin, i_end, tau=1.0, flags=DEFAULT_FLAGS, threads=1):
+        """(rho, n_valid) of template particles [i_begin, i_end) about centre c with
+        axes r over the points with mask != 0 (Eq. normallh)."""
+        lib = _load()
+        pts, pp = _d(pts)
+        mask, pm = _i(mask)
+        c, pc = _d(c)
+        r, pr = _d(r)
+        omega, pom = _f(omega)
+        N = omega.shape[1]
+        _, pdim = _i(self.dims)
+        _, por = _d(self.origin)
+        rho, prho = _d(np.zeros(N))
+        nval, pnv = _i(np.zeros(N, np.int32))
+        delta, pdl = _d(np.zeros(6 * N))
+        lib.or_fitness_particles(self.F.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pdim, self.voxel, por, pp,
+                                 pm, pts.shape[0], pc, pr, pom, N, int(i_begin), int(i_end), float(tau), int(flags),
+                                 int(threads), prho, pnv, pdl)
+        return rho[i_begin:i_end].copy(), nval[i_begin:i_end].copy()
 
 
 def pst_update(rho, delta, rho_ref, r_prev, beta=0.1, eps=1e-3):

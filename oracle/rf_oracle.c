@@ -30,11 +30,20 @@
  *  64 RIGHT_MULT   particle offset applied in the camera frame (T_c * T_delta)
  * 128 CELL_MARGIN  overlap set: the re-projected point must lie inside frame
  *                  t-1's image by the footprint of one TSDF cell (sqrt(3) voxels)
+ * 256 APS_WITH_CENTRE  the centre particle (particle 0, s*_{k-1} itself) is an
+ *                  APS candidate like every other particle
+ *
+ * Threads: or_fitness_particles, the *_mt frame functions and
+ * or_tsdf_integrate_mt may split independent items (particles, voxel slices)
+ * over threads for speed; every item is computed by the same plain loop and
+ * every reduction stays sequential, so the results do not depend on the
+ * thread count.
  *
  * Functions whose result has no independent pin say so in their comment;
  * every other function is pinned by tests/test_oracle_*.py.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -47,6 +56,7 @@
 #define OR_L1 32
 #define OR_RIGHT_MULT 64
 #define OR_CELL_MARGIN 128
+#define OR_APS_WITH_CENTRE 256
 
 #define OR_OK 0
 #define OR_ERR_ARG -1
@@ -413,82 +423,200 @@ int or_pst_update(int N, const double *rho, const double *delta, double rho_ref,
 #define OR_TRACE_STRIDE 40
 /* trace row per iteration k (doubles):
  *  0 k, 1 |O_k|, 2 |APS|, 3 rho_ref, 4 rho_tilde, 5 rho_max, 6 argmax,
- *  7..13 s*_k (pose), 14..19 r_k, 20..25 delta_bar, 26 min_i |rho_i - rho_ref|,
- *  27 min overlap rounding margin, 28 stop reason (0 running, 1 empty twice,
- *  2 small step, 3 k_max, 4 empty overlap), 29 second-largest rho            */
+ *  7..13 s*_k (pose), 14..19 r_k, 20..25 delta_bar, 26 min_i |rho_i - rho_ref|
+ *  over the APS candidates, 27 min overlap rounding margin (px), 28 stop reason
+ *  (0 running, 1 empty twice, 2 small step, 3 k_max, 4 empty overlap),
+ *  29 second-largest rho, 30 level, 31 particles scored, 32 corner case of
+ *  Sec. 4 "PST update" (0 none, 1 no TSDF yet, 2 empty APS), 33 valid samples
+ *  summed over all particles, 34 consecutive empty APS after this iteration,
+ *  35 points whose overlap decision lies within OR_TIE_PX of its threshold,
+ *  36 candidates whose fitness lies within OR_TIE_RHO of the APS threshold,
+ *  37 sensitivity of delta_bar to the weights: sum_APS max_d |delta_i,d -
+ *  delta_bar_d| / sum_APS w_i (so an error e in every weight moves delta_bar by
+ *  at most e times this), 38 max_d |delta_bar_d| (the small-step statistic),
+ *  39 the same sensitivity for independent weight errors: sqrt(sum_APS max_d
+ *  |delta_i,d - delta_bar_d|^2) / sum_APS w_i                                */
+#define OR_TIE_PX 1e-3
+#define OR_TIE_RHO 1e-5
+
+/* State of Algorithm 1 between two iterations (doubles):
+ *  0..6 c_{k-1} = s*_{k-1}, 7..12 r_{k-1}, 13 rho(s*_{k-1}) by Eq. wafit (the
+ *  carried APS threshold), 14 consecutive empty APS so far, 15 k, the iteration
+ *  about to run (1-based). */
+#define OR_STATE_LEN 16
+
+/* Fitness of particles [0, Nl) of the template about centre c with axes r:
+ * delta_i = r . omega_i, pose_i = c (+) delta_i, rho_i and the valid-sample
+ * count by or_fitness over the points with mask != 0.  Particles are
+ * independent, so the work may be split over threads (each thread runs the
+ * plain per-particle loop on its own particles); the results do not depend on
+ * the thread count. */
+typedef struct {
+    const double *F;
+    const int *dim;
+    double voxel;
+    const double *origin;
+    const double *pts;
+    const int *mask;
+    int M;
+    const double *c, *r;
+    const float *omega;
+    int N, i0, i1;
+    double tau;
+    int flags;
+    double *rho, *delta;
+    int *nval;
+} or_fit_job;
+
+static void *or_fit_worker(void *arg)
+{
+    or_fit_job *j = (or_fit_job *)arg;
+    for (int i = j->i0; i < j->i1; ++i) {
+        double pose[7], S;
+        int n, nO;
+        for (int d = 0; d < 6; ++d)
+            j->delta[6 * (size_t)i + d] = j->r[d] * j->omega[(size_t)d * j->N + i];
+        or_compose_offset(j->c, j->delta + 6 * (size_t)i, j->flags, pose);
+        or_fitness(j->F, j->dim, j->voxel, j->origin, j->pts, j->mask, j->M, pose, j->tau, j->flags, &S, &n, &nO,
+                   &j->rho[i]);
+        j->nval[i] = n;
+    }
+    return NULL;
+}
+
+/* rho[i], nval[i] and delta[6i..6i+5] for i in [i_begin, i_end). */
+void or_fitness_particles(const double *F, const int dim[3], double voxel, const double origin[3], const double *pts,
+                          const int *mask, int M, const double c[7], const double r[6], const float *omega, int N,
+                          int i_begin, int i_end, double tau, int flags, int nthreads, double *rho, int *nval,
+                          double *delta)
+{
+    int nt = nthreads < 1 ? 1 : nthreads;
+    int count = i_end - i_begin;
+    if (count <= 0)
+        return;
+    if (nt > count)
+        nt = count;
+    or_fit_job jobs[256];
+    pthread_t th[256];
+    if (nt > 256)
+        nt = 256;
+    for (int t = 0; t < nt; ++t) {
+        or_fit_job *j = &jobs[t];
+        j->F = F;
+        j->dim = dim;
+        j->voxel = voxel;
+        j->origin = origin;
+        j->pts = pts;
+        j->mask = mask;
+        j->M = M;
+        j->c = c;
+        j->r = r;
+        j->omega = omega;
+        j->N = N;
+        j->i0 = i_begin + (int)((long long)count * t / nt);
+        j->i1 = i_begin + (int)((long long)count * (t + 1) / nt);
+        j->tau = tau;
+        j->flags = flags;
+        j->rho = rho;
+        j->delta = delta;
+        j->nval = nval;
+    }
+    if (nt == 1) {
+        or_fit_worker(&jobs[0]);
+        return;
+    }
+    int started = 0;
+    for (int t = 1; t < nt; ++t) {
+        if (pthread_create(&th[t], NULL, or_fit_worker, &jobs[t]) != 0)
+            break;
+        started = t;
+    }
+    or_fit_worker(&jobs[0]);
+    for (int t = started + 1; t < nt; ++t) /* threads that could not start run here */
+        or_fit_worker(&jobs[t]);
+    for (int t = 1; t <= started; ++t)
+        pthread_join(th[t], NULL);
+}
 
 /*
- * Inputs: the volume, the frame's points (or_unproject output, M of them), the
- * previous frame's full-resolution depth and final pose (for Eq. validness),
- * the initial centre c0 and axis lengths r0 (Sec. 4 "PST initialization"),
- * the template omega (6 x N, structure of arrays, row 0 = origin), the
- * parameters.  Outputs: final pose s*, the axis lengths after iteration 1
- * (r_1, handed to the next frame), the trace, the number of iterations.
- * Loop order follows Algorithm 1 with the readings: iteration k evaluates the
- * PST centred at c_{k-1} with axes r_{k-1}; rho_ref = rho of particle 0 at
- * k = 1 (and with RHO_REF_CENTER), else the carried Eq. wafit value; the APS
- * is drawn from particles 1..N-1 (particle 0 is s*_{k-1} itself); stop on
- * two consecutive empty APS, a step below stop_eps in all six dimensions, or
- * k = k_max (Sec. 4 "Convergence criteria").
- * Returns 0, or OR_ERR_EMPTY if |O_k| = 0 (the pose then stays s*_{k-1}).
+ * One iteration k of Algorithm 1 (state layout above), on Nl <= N particles
+ * (the first Nl rows of the template omega, 6 x N structure of arrays, row 0 =
+ * origin) and M points (or_unproject output):
+ *  1. O_k with s*_{k-1} = c_{k-1} (Eq. validness; all valid points without OVERLAP)
+ *  2. fitness of every particle c_{k-1} (+) (r_{k-1} . omega_i) (Eq. normallh)
+ *  3. APS threshold rho(s*_{k-1}): particle 0 when k = 1, RHO_REF_CENTER or
+ *     centre_ref != 0, else the carried Eq. wafit value (readings 7-8)
+ *  4. APS = candidates strictly above it (particles 1..Nl-1, plus particle 0
+ *     with APS_WITH_CENTRE); or_pst_update: Eq. ebs, wafit, rsdir, rsinter,
+ *     momentum, and the empty-APS corner case of Sec. 4
+ *  5. first corner case of Sec. 4 ("TSDF has not been built"): when no
+ *     particle has a single valid TSDF sample the likelihood cannot be
+ *     evaluated; the iteration then keeps s*, uses rho = 0.5 and the isotropic
+ *     attractor v = 1, r_hat = 0.5 v + eps, and counts as an empty APS
+ *  6. stop rules of Sec. 4: two consecutive empty APS, a step below stop_eps
+ *     in all six dimensions, or k = k_max; an empty O_k stops with code 4.
+ * Updates `state` (unless O_k is empty) and writes the trace row tr (may be
+ * NULL).  Returns the stop code (0 = continue), or OR_ERR_ARG.
  */
-int or_pfo_frame(const double *F, const int dim[3], double voxel, const double origin[3], const double *pts, int M,
-                 const float *prev_depth, int W, int H, double fx, double fy, double cx, double cy, double z_min,
-                 double z_max, const double pose_prev[7], const double c0[7], const double r0[6],
-                 const float *omega, int N, double tau, double beta, double eps, double stop_eps, int k_max,
-                 int flags, double pose_out[7], double r1_out[6], double *trace, int *iters_out)
+int or_pfo_step(const double *F, const int dim[3], double voxel, const double origin[3], const double *pts, int M,
+                int Nl, const float *prev_depth, int W, int H, double fx, double fy, double cx, double cy,
+                double z_min, double z_max, const double pose_prev[7], const float *omega, int N, double tau,
+                double beta, double eps, double stop_eps, int k_max, int flags, int centre_ref, int nthreads,
+                double *state, double *tr)
 {
-    if (N < 1 || k_max < 1)
+    if (Nl < 1 || Nl > N || M < 0)
         return OR_ERR_ARG;
     for (int d = 0; d < 6; ++d)
         if (omega[(size_t)d * N] != 0.0f)
             return OR_ERR_ARG; /* row 0 must be the origin (reading 8) */
+    double c[7], r[6];
+    memcpy(c, state, sizeof c);
+    memcpy(r, state + 7, sizeof r);
+    const double rho_carry = state[13];
+    int empty_run = (int)state[14];
+    const int k = (int)state[15];
     int *mask = (int *)malloc(sizeof(int) * (size_t)(M > 0 ? M : 1));
     double *margin = (double *)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1));
-    double *rho = (double *)malloc(sizeof(double) * (size_t)N);
-    double *delta = (double *)malloc(sizeof(double) * 6 * (size_t)N);
-    double c[7], r[6], rho_carry = 0.0;
-    memcpy(c, c0, sizeof c);
-    memcpy(r, r0, sizeof r);
-    int empty_run = 0, status = OR_OK, k = 0;
-    for (k = 1; k <= k_max; ++k) {
-        /* O_k with s*_{k-1} = c_{k-1} */
-        int nO = 0;
-        double min_margin = INFINITY;
-        if (flags & OR_OVERLAP) {
-            nO = or_overlap(pts, M, prev_depth, W, H, fx, fy, cx, cy, z_min, z_max, c, pose_prev,
-                            (flags & OR_CELL_MARGIN) ? sqrt(3.0) * voxel : 0.0, mask, margin);
-            for (int j = 0; j < M; ++j)
-                if (pts[4 * (size_t)j + 3] != 0.0 && margin[j] < min_margin)
+    double *rho = (double *)malloc(sizeof(double) * (size_t)Nl);
+    int *nval = (int *)malloc(sizeof(int) * (size_t)Nl);
+    double *delta = (double *)malloc(sizeof(double) * 6 * (size_t)Nl);
+    /* 1. O_k */
+    int nO = 0, fragile_px = 0;
+    double min_margin = INFINITY;
+    if (flags & OR_OVERLAP) {
+        nO = or_overlap(pts, M, prev_depth, W, H, fx, fy, cx, cy, z_min, z_max, c, pose_prev,
+                        (flags & OR_CELL_MARGIN) ? sqrt(3.0) * voxel : 0.0, mask, margin);
+        for (int j = 0; j < M; ++j)
+            if (pts[4 * (size_t)j + 3] != 0.0) {
+                if (margin[j] < min_margin)
                     min_margin = margin[j];
-        } else {
-            for (int j = 0; j < M; ++j) {
-                mask[j] = pts[4 * (size_t)j + 3] != 0.0;
-                nO += mask[j];
+                if (margin[j] < OR_TIE_PX)
+                    ++fragile_px;
             }
+    } else {
+        for (int j = 0; j < M; ++j) {
+            mask[j] = pts[4 * (size_t)j + 3] != 0.0;
+            nO += mask[j];
         }
-        double *tr = trace ? trace + OR_TRACE_STRIDE * (size_t)(k - 1) : NULL;
-        if (nO == 0) {
-            status = OR_ERR_EMPTY;
-            if (tr) {
-                memset(tr, 0, sizeof(double) * OR_TRACE_STRIDE);
-                tr[0] = k;
-                tr[28] = 4;
-            }
-            break;
+    }
+    int stop = 0;
+    if (nO == 0) {
+        stop = 4;
+        if (tr) {
+            memset(tr, 0, sizeof(double) * OR_TRACE_STRIDE);
+            tr[0] = k;
+            tr[28] = 4;
+            tr[31] = Nl;
+            tr[34] = empty_run;
         }
-        /* fitness of every particle (Eq. normallh) */
-        double rho_max = -1.0, rho_2nd = -1.0;
+    } else {
+        /* 2. fitness of every particle */
+        or_fitness_particles(F, dim, voxel, origin, pts, mask, M, c, r, omega, N, 0, Nl, tau, flags, nthreads, rho,
+                             nval, delta);
+        double rho_max = -1.0, rho_2nd = -1.0, valid = 0.0;
         int argmax = 0;
-        for (int i = 0; i < N; ++i) {
-            double om[6], pose[7], S;
-            int n, nOi;
-            for (int d = 0; d < 6; ++d) {
-                om[d] = omega[(size_t)d * N + i];
-                delta[6 * (size_t)i + d] = r[d] * om[d];
-            }
-            or_compose_offset(c, delta + 6 * (size_t)i, flags, pose);
-            or_fitness(F, dim, voxel, origin, pts, mask, M, pose, tau, flags, &S, &n, &nOi, &rho[i]);
+        for (int i = 0; i < Nl; ++i) {
+            valid += (double)nval[i];
             if (rho[i] > rho_max) {
                 rho_2nd = rho_max;
                 rho_max = rho[i];
@@ -497,16 +625,50 @@ int or_pfo_frame(const double *F, const int dim[3], double voxel, const double o
                 rho_2nd = rho[i];
             }
         }
-        double rho_ref = (k == 1 || (flags & OR_RHO_REF_CENTER)) ? rho[0] : rho_carry;
+        /* 3. threshold */
+        const double rho_ref = (k == 1 || (flags & OR_RHO_REF_CENTER) || centre_ref) ? rho[0] : rho_carry;
+        /* 4. APS over the candidates: particles 1..Nl-1 (particle 0 is s*_{k-1} itself) */
+        const int first = (flags & OR_APS_WITH_CENTRE) ? 0 : 1;
         double min_gap = INFINITY;
-        for (int i = 0; i < N; ++i)
-            if (fabs(rho[i] - rho_ref) < min_gap && i != 0)
-                min_gap = fabs(rho[i] - rho_ref);
+        int ties = 0;
+        for (int i = first; i < Nl; ++i) {
+            double g = fabs(rho[i] - rho_ref);
+            if (g < min_gap)
+                min_gap = g;
+            if (g < OR_TIE_RHO)
+                ++ties;
+        }
         double dbar[6], rho_tilde, r_new[6];
-        /* the APS holds particles better than s*_{k-1}; particle 0 (zero offset) is
-         * s*_{k-1} itself, so it is no candidate (it only passes rho_ref when that is
-         * the Eq. wafit approximation) */
-        int n_aps = or_pst_update(N - 1, rho + 1, delta + 6, rho_ref, r, beta, eps, dbar, &rho_tilde, r_new);
+        int n_aps, corner;
+        if (valid == 0.0) {
+            /* 5. no TSDF sample anywhere: rho = 0.5, v = 1 (not normalised) */
+            n_aps = 0;
+            corner = 1;
+            rho_tilde = 0.5;
+            for (int d = 0; d < 6; ++d) {
+                dbar[d] = 0.0;
+                r_new[d] = beta * r[d] + (1.0 - beta) * (0.5 * 1.0 + eps);
+            }
+        } else {
+            n_aps = or_pst_update(Nl - first, rho + first, delta + 6 * (size_t)first, rho_ref, r, beta, eps, dbar,
+                                  &rho_tilde, r_new);
+            corner = n_aps == 0 ? 2 : 0;
+        }
+        double sens = 0.0, sens2 = 0.0;
+        if (n_aps > 0) {
+            double sw = 0.0;
+            for (int i = first; i < Nl; ++i)
+                if (rho[i] > rho_ref) {
+                    double dev = 0.0;
+                    for (int d = 0; d < 6; ++d)
+                        dev = fmax(dev, fabs(delta[6 * (size_t)i + d] - dbar[d]));
+                    sens += dev;
+                    sens2 += dev * dev;
+                    sw += rho[i] - rho_ref;
+                }
+            sens /= sw;
+            sens2 = sqrt(sens2) / sw;
+        }
         double s_new[7];
         if (n_aps > 0) {
             or_compose_offset(c, dbar, flags, s_new);
@@ -515,21 +677,20 @@ int or_pfo_frame(const double *F, const int dim[3], double voxel, const double o
             memcpy(s_new, c, sizeof s_new);
             ++empty_run;
         }
-        rho_carry = rho_tilde;
-        memcpy(c, s_new, sizeof c);
-        memcpy(r, r_new, sizeof r);
-        if (k == 1)
-            memcpy(r1_out, r, sizeof r);
+        /* 6. stop rules */
         double step = 0.0;
         for (int d = 0; d < 6; ++d)
             step = fmax(step, fabs(dbar[d]));
-        int stop = 0;
         if (empty_run >= 2)
             stop = 1;
         else if (n_aps > 0 && step < stop_eps)
             stop = 2;
         else if (k == k_max)
             stop = 3;
+        memcpy(state, s_new, sizeof(double) * 7);
+        memcpy(state + 7, r_new, sizeof(double) * 6);
+        state[13] = rho_tilde;
+        state[14] = empty_run;
         if (tr) {
             tr[0] = k;
             tr[1] = nO;
@@ -539,30 +700,138 @@ int or_pfo_frame(const double *F, const int dim[3], double voxel, const double o
             tr[5] = rho_max;
             tr[6] = argmax;
             for (int a = 0; a < 7; ++a)
-                tr[7 + a] = c[a];
+                tr[7 + a] = s_new[a];
             for (int d = 0; d < 6; ++d) {
-                tr[14 + d] = r[d];
+                tr[14 + d] = r_new[d];
                 tr[20 + d] = dbar[d];
             }
             tr[26] = min_gap;
             tr[27] = min_margin;
             tr[28] = stop;
             tr[29] = rho_2nd;
+            tr[31] = Nl;
+            tr[32] = corner;
+            tr[33] = valid;
+            tr[34] = empty_run;
+            tr[35] = fragile_px;
+            tr[36] = ties;
+            tr[37] = sens;
+            tr[38] = step;
+            tr[39] = sens2;
         }
+    }
+    if (tr)
+        tr[35] = fragile_px;
+    state[15] = k + 1;
+    free(mask);
+    free(margin);
+    free(rho);
+    free(nval);
+    free(delta);
+    return stop;
+}
+
+/*
+ * Algorithm 1 with L (particle count, depth stride) levels used in turn (Sec. 4
+ * "Multi-resolution PST"; L = 1 is the plain algorithm): iteration k runs
+ * or_pfo_step on level l = (k - 1) mod L, i.e. the first level_n[l] rows of the
+ * template and the points level_pts[l] (level_M[l] of them).  With L > 1 the
+ * fitness of consecutive iterations is normalised over different point sets,
+ * so the APS threshold is the centre particle's fitness in the current
+ * iteration (reading 17).  The PST starts at c0 with axes r0 (Sec. 4 "PST
+ * initialization").  Outputs: the final pose s*, the axis lengths after
+ * iteration 1 (r_1, handed to the next frame; r0 if O_1 is empty), the trace
+ * (k_max rows of OR_TRACE_STRIDE, may be NULL) and the iteration count.
+ * Returns 0, OR_ERR_EMPTY if some |O_k| = 0 (the pose then stays s*_{k-1}), or
+ * OR_ERR_ARG.
+ */
+int or_pfo_frame_sched_mt(const double *F, const int dim[3], double voxel, const double origin[3], int L,
+                          const int *level_n, const double *const *level_pts, const int *level_M,
+                          const float *prev_depth, int W, int H, double fx, double fy, double cx, double cy,
+                          double z_min, double z_max, const double pose_prev[7], const double c0[7],
+                          const double r0[6], const float *omega, int N, double tau, double beta, double eps,
+                          double stop_eps, int k_max, int flags, int nthreads, double pose_out[7], double r1_out[6],
+                          double *trace, int *iters_out)
+{
+    if (L < 1 || N < 1 || k_max < 1)
+        return OR_ERR_ARG;
+    for (int l = 0; l < L; ++l)
+        if (level_n[l] < 1 || level_n[l] > N)
+            return OR_ERR_ARG;
+    double state[OR_STATE_LEN];
+    memcpy(state, c0, sizeof(double) * 7);
+    memcpy(state + 7, r0, sizeof(double) * 6);
+    state[13] = 0.0;
+    state[14] = 0.0;
+    state[15] = 1.0;
+    memcpy(r1_out, r0, sizeof(double) * 6);
+    int status = OR_OK, k;
+    for (k = 1; k <= k_max; ++k) {
+        const int l = (k - 1) % L;
+        double *tr = trace ? trace + OR_TRACE_STRIDE * (size_t)(k - 1) : NULL;
+        int stop = or_pfo_step(F, dim, voxel, origin, level_pts[l], level_M[l], level_n[l], prev_depth, W, H, fx,
+                               fy, cx, cy, z_min, z_max, pose_prev, omega, N, tau, beta, eps, stop_eps, k_max, flags,
+                               L > 1, nthreads, state, tr);
+        if (stop < 0)
+            return stop;
+        if (tr)
+            tr[30] = l;
+        if (stop == 4) {
+            status = OR_ERR_EMPTY;
+            break;
+        }
+        if (k == 1)
+            memcpy(r1_out, state + 7, sizeof(double) * 6);
         if (stop)
             break;
     }
     if (k > k_max)
         k = k_max;
-    memcpy(pose_out, c, sizeof c);
-    if (k == 1 && status == OR_ERR_EMPTY)
-        memcpy(r1_out, r0, sizeof r);
+    memcpy(pose_out, state, sizeof(double) * 7);
     *iters_out = k;
-    free(mask);
-    free(margin);
-    free(rho);
-    free(delta);
     return status;
+}
+
+/* Single-threaded multi-resolution frame (see or_pfo_frame_sched_mt). */
+int or_pfo_frame_sched(const double *F, const int dim[3], double voxel, const double origin[3], int L,
+                       const int *level_n, const double *const *level_pts, const int *level_M,
+                       const float *prev_depth, int W, int H, double fx, double fy, double cx, double cy,
+                       double z_min, double z_max, const double pose_prev[7], const double c0[7], const double r0[6],
+                       const float *omega, int N, double tau, double beta, double eps, double stop_eps, int k_max,
+                       int flags, double pose_out[7], double r1_out[6], double *trace, int *iters_out)
+{
+    return or_pfo_frame_sched_mt(F, dim, voxel, origin, L, level_n, level_pts, level_M, prev_depth, W, H, fx, fy, cx,
+                                 cy, z_min, z_max, pose_prev, c0, r0, omega, N, tau, beta, eps, stop_eps, k_max,
+                                 flags, 1, pose_out, r1_out, trace, iters_out);
+}
+
+/*
+ * Algorithm 1 for one frame on one point set and the whole template:
+ * or_pfo_frame_sched_mt with a single level (see there for inputs, outputs and
+ * the readings).  nthreads splits the per-particle fitness loop only.
+ */
+int or_pfo_frame_mt(const double *F, const int dim[3], double voxel, const double origin[3], const double *pts, int M,
+                    const float *prev_depth, int W, int H, double fx, double fy, double cx, double cy, double z_min,
+                    double z_max, const double pose_prev[7], const double c0[7], const double r0[6],
+                    const float *omega, int N, double tau, double beta, double eps, double stop_eps, int k_max,
+                    int flags, int nthreads, double pose_out[7], double r1_out[6], double *trace, int *iters_out)
+{
+    const int level_n[1] = {N}, level_M[1] = {M};
+    const double *level_pts[1] = {pts};
+    return or_pfo_frame_sched_mt(F, dim, voxel, origin, 1, level_n, level_pts, level_M, prev_depth, W, H, fx, fy, cx,
+                                 cy, z_min, z_max, pose_prev, c0, r0, omega, N, tau, beta, eps, stop_eps, k_max,
+                                 flags, nthreads, pose_out, r1_out, trace, iters_out);
+}
+
+int or_pfo_frame(const double *F, const int dim[3], double voxel, const double origin[3], const double *pts, int M,
+                 const float *prev_depth, int W, int H, double fx, double fy, double cx, double cy, double z_min,
+                 double z_max, const double pose_prev[7], const double c0[7], const double r0[6],
+                 const float *omega, int N, double tau, double beta, double eps, double stop_eps, int k_max,
+                 int flags, double pose_out[7], double r1_out[6], double *trace, int *iters_out)
+{
+    return or_pfo_frame_mt(F, dim, voxel, origin, pts, M, prev_depth, W, H, fx, fy, cx, cy, z_min, z_max, pose_prev,
+                           c0, r0, omega, N, tau, beta, eps, stop_eps, k_max, flags, 1, pose_out, r1_out, trace,
+                           iters_out);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -597,45 +866,117 @@ double or_quantize(double F, int qmode)
  * pixel; with a valid depth D there, sdf = D - z_cam; voxels with sdf < -trunc
  * are untouched; otherwise f = min(1, sdf / trunc) and
  *   F <- (W F + f) / (W + 1),   W <- min(W + 1, w_max).
- * F is rounded to the storage type after every update (qmode).
+ * F is rounded to the storage type after every update (qmode).  Slices z in
+ * [z0, z1) only (the whole volume: 0, dim[2]).
  */
+typedef struct {
+    double *F;
+    int *Wt;
+    const int *dim;
+    double voxel;
+    const double *origin;
+    double trunc;
+    int w_max, qmode;
+    const float *depth;
+    int W, H;
+    double fx, fy, cx, cy, z_min, z_max;
+    const double *pose;
+    int z0, z1;
+} or_integrate_job;
+
+static void *or_integrate_slices(void *arg)
+{
+    const or_integrate_job *j = (const or_integrate_job *)arg;
+    const int *dim = j->dim;
+    double R[9];
+    or_quat_to_rot(j->pose, R);
+    for (int k = j->z0; k < j->z1; ++k)
+        for (int jy = 0; jy < dim[1]; ++jy)
+            for (int i = 0; i < dim[0]; ++i) {
+                double pw[3] = {j->origin[0] + j->voxel * (i + 0.5), j->origin[1] + j->voxel * (jy + 0.5),
+                                j->origin[2] + j->voxel * (k + 0.5)};
+                double pc[3];
+                apply_pose_inverse(R, j->pose + 4, pw, pc);
+                if (!(pc[2] > 0.0))
+                    continue;
+                double u = floor(j->fx * pc[0] / pc[2] + j->cx + 0.5);
+                double v = floor(j->fy * pc[1] / pc[2] + j->cy + 0.5);
+                if (u < 0.0 || u >= (double)j->W || v < 0.0 || v >= (double)j->H)
+                    continue;
+                double D = j->depth[(size_t)v * j->W + (size_t)u];
+                if (!(D > j->z_min && D <= j->z_max))
+                    continue;
+                double sdf = D - pc[2];
+                if (sdf < -j->trunc)
+                    continue;
+                double f = sdf / j->trunc;
+                if (f > 1.0)
+                    f = 1.0;
+                size_t idx = (size_t)i + (size_t)dim[0] * ((size_t)jy + (size_t)dim[1] * (size_t)k);
+                int w_old = j->Wt[idx];
+                double F_old = isnan(j->F[idx]) ? 0.0 : j->F[idx];
+                if (isnan(j->F[idx]))
+                    w_old = 0;
+                double F_new = ((double)w_old * F_old + f) / (double)(w_old + 1);
+                j->F[idx] = or_quantize(F_new, j->qmode);
+                j->Wt[idx] = (w_old + 1 < j->w_max) ? w_old + 1 : j->w_max;
+            }
+    return NULL;
+}
+
+/* The update of every voxel, the z slices split over nthreads threads (each
+ * voxel is updated by the same plain code whatever the split). */
+void or_tsdf_integrate_mt(double *F, int *Wt, const int dim[3], double voxel, const double origin[3], double trunc,
+                          int w_max, int qmode, const float *depth, int W, int H, double fx, double fy, double cx,
+                          double cy, double z_min, double z_max, const double pose[7], int nthreads)
+{
+    int nt = nthreads < 1 ? 1 : (nthreads > 256 ? 256 : nthreads);
+    if (nt > dim[2])
+        nt = dim[2];
+    or_integrate_job jobs[256];
+    pthread_t th[256];
+    for (int t = 0; t < nt; ++t) {
+        or_integrate_job *j = &jobs[t];
+        j->F = F;
+        j->Wt = Wt;
+        j->dim = dim;
+        j->voxel = voxel;
+        j->origin = origin;
+        j->trunc = trunc;
+        j->w_max = w_max;
+        j->qmode = qmode;
+        j->depth = depth;
+        j->W = W;
+        j->H = H;
+        j->fx = fx;
+        j->fy = fy;
+        j->cx = cx;
+        j->cy = cy;
+        j->z_min = z_min;
+        j->z_max = z_max;
+        j->pose = pose;
+        j->z0 = (int)((long long)dim[2] * t / nt);
+        j->z1 = (int)((long long)dim[2] * (t + 1) / nt);
+    }
+    int started = 0;
+    for (int t = 1; t < nt; ++t) {
+        if (pthread_create(&th[t], NULL, or_integrate_slices, &jobs[t]) != 0)
+            break;
+        started = t;
+    }
+    or_integrate_slices(&jobs[0]);
+    for (int t = started + 1; t < nt; ++t)
+        or_integrate_slices(&jobs[t]);
+    for (int t = 1; t <= started; ++t)
+        pthread_join(th[t], NULL);
+}
+
 void or_tsdf_integrate(double *F, int *Wt, const int dim[3], double voxel, const double origin[3], double trunc,
                        int w_max, int qmode, const float *depth, int W, int H, double fx, double fy, double cx,
                        double cy, double z_min, double z_max, const double pose[7])
 {
-    double R[9];
-    or_quat_to_rot(pose, R);
-    for (int k = 0; k < dim[2]; ++k)
-        for (int j = 0; j < dim[1]; ++j)
-            for (int i = 0; i < dim[0]; ++i) {
-                double pw[3] = {origin[0] + voxel * (i + 0.5), origin[1] + voxel * (j + 0.5),
-                                origin[2] + voxel * (k + 0.5)};
-                double pc[3];
-                apply_pose_inverse(R, pose + 4, pw, pc);
-                if (!(pc[2] > 0.0))
-                    continue;
-                double u = floor(fx * pc[0] / pc[2] + cx + 0.5);
-                double v = floor(fy * pc[1] / pc[2] + cy + 0.5);
-                if (u < 0.0 || u >= (double)W || v < 0.0 || v >= (double)H)
-                    continue;
-                double D = depth[(size_t)v * W + (size_t)u];
-                if (!(D > z_min && D <= z_max))
-                    continue;
-                double sdf = D - pc[2];
-                if (sdf < -trunc)
-                    continue;
-                double f = sdf / trunc;
-                if (f > 1.0)
-                    f = 1.0;
-                size_t idx = (size_t)i + (size_t)dim[0] * ((size_t)j + (size_t)dim[1] * (size_t)k);
-                int w_old = Wt[idx];
-                double F_old = isnan(F[idx]) ? 0.0 : F[idx];
-                if (isnan(F[idx]))
-                    w_old = 0;
-                double F_new = ((double)w_old * F_old + f) / (double)(w_old + 1);
-                F[idx] = or_quantize(F_new, qmode);
-                Wt[idx] = (w_old + 1 < w_max) ? w_old + 1 : w_max;
-            }
+    or_tsdf_integrate_mt(F, Wt, dim, voxel, origin, trunc, w_max, qmode, depth, W, H, fx, fy, cx, cy, z_min, z_max,
+                         pose, 1);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -936,161 +1277,4 @@ void or_tsdf_integrate_ambiguity(const int dim[3], double voxel, const double or
                 }
                 ambig[idx] = a;
             }
-}
-
-/* ------------------------------------------------------------------------- */
-/* Multi-resolution PST alternation (Sec. 4 "Multi-resolution PST").          */
-/* ------------------------------------------------------------------------- */
-
-/*
- * Algorithm 1 with L (particle count, depth stride) levels used in turn:
- * iteration k uses level l = (k - 1) mod L, i.e. the first level_n[l] rows of
- * the template and the points unprojected at that level's stride
- * (level_pts[l], level_M[l] points).  Readings: with L > 1 the fitness of
- * consecutive iterations is normalised over different point sets, so the APS
- * threshold is the fitness of the centre particle in the current iteration
- * (particle 0); with L = 1 the rule of or_pfo_frame applies.  Everything else
- * (overlap with s*_{k-1}, Eq. ebs / wafit / rsdir / rsinter / momentum, the
- * corner cases and stop rules) is that of or_pfo_frame.  Same outputs.
- */
-int or_pfo_frame_sched(const double *F, const int dim[3], double voxel, const double origin[3], int L,
-                       const int *level_n, const double *const *level_pts, const int *level_M,
-                       const float *prev_depth, int W, int H, double fx, double fy, double cx, double cy,
-                       double z_min, double z_max, const double pose_prev[7], const double c0[7], const double r0[6],
-                       const float *omega, int N, double tau, double beta, double eps, double stop_eps, int k_max,
-                       int flags, double pose_out[7], double r1_out[6], double *trace, int *iters_out)
-{
-    if (L < 1 || N < 1 || k_max < 1)
-        return OR_ERR_ARG;
-    int M_max = 1, N_lev_max = 1;
-    for (int l = 0; l < L; ++l) {
-        if (level_n[l] < 1 || level_n[l] > N)
-            return OR_ERR_ARG;
-        if (level_M[l] > M_max)
-            M_max = level_M[l];
-        if (level_n[l] > N_lev_max)
-            N_lev_max = level_n[l];
-    }
-    for (int d = 0; d < 6; ++d)
-        if (omega[(size_t)d * N] != 0.0f)
-            return OR_ERR_ARG;
-    int *mask = (int *)malloc(sizeof(int) * (size_t)M_max);
-    double *margin = (double *)malloc(sizeof(double) * (size_t)M_max);
-    double *rho = (double *)malloc(sizeof(double) * (size_t)N_lev_max);
-    double *delta = (double *)malloc(sizeof(double) * 6 * (size_t)N_lev_max);
-    double c[7], r[6], rho_carry = 0.0;
-    memcpy(c, c0, sizeof c);
-    memcpy(r, r0, sizeof r);
-    int empty_run = 0, status = OR_OK, k = 0;
-    for (k = 1; k <= k_max; ++k) {
-        const int l = (k - 1) % L;
-        const int Nl = level_n[l], M = level_M[l];
-        const double *pts = level_pts[l];
-        int nO = 0;
-        double min_margin = INFINITY;
-        if (flags & OR_OVERLAP) {
-            nO = or_overlap(pts, M, prev_depth, W, H, fx, fy, cx, cy, z_min, z_max, c, pose_prev,
-                            (flags & OR_CELL_MARGIN) ? sqrt(3.0) * voxel : 0.0, mask, margin);
-            for (int j = 0; j < M; ++j)
-                if (pts[4 * (size_t)j + 3] != 0.0 && margin[j] < min_margin)
-                    min_margin = margin[j];
-        } else {
-            for (int j = 0; j < M; ++j) {
-                mask[j] = pts[4 * (size_t)j + 3] != 0.0;
-                nO += mask[j];
-            }
-        }
-        double *tr = trace ? trace + OR_TRACE_STRIDE * (size_t)(k - 1) : NULL;
-        if (nO == 0) {
-            status = OR_ERR_EMPTY;
-            if (tr) {
-                memset(tr, 0, sizeof(double) * OR_TRACE_STRIDE);
-                tr[0] = k;
-                tr[28] = 4;
-            }
-            break;
-        }
-        double rho_max = -1.0, rho_2nd = -1.0;
-        int argmax = 0;
-        for (int i = 0; i < Nl; ++i) {
-            double pose[7], S;
-            int n, nOi;
-            for (int d = 0; d < 6; ++d)
-                delta[6 * (size_t)i + d] = r[d] * omega[(size_t)d * N + i];
-            or_compose_offset(c, delta + 6 * (size_t)i, flags, pose);
-            or_fitness(F, dim, voxel, origin, pts, mask, M, pose, tau, flags, &S, &n, &nOi, &rho[i]);
-            if (rho[i] > rho_max) {
-                rho_2nd = rho_max;
-                rho_max = rho[i];
-                argmax = i;
-            } else if (rho[i] > rho_2nd) {
-                rho_2nd = rho[i];
-            }
-        }
-        const int centre_ref = (k == 1) || (flags & OR_RHO_REF_CENTER) || (L > 1);
-        double rho_ref = centre_ref ? rho[0] : rho_carry;
-        double min_gap = INFINITY;
-        for (int i = 1; i < Nl; ++i)
-            if (fabs(rho[i] - rho_ref) < min_gap)
-                min_gap = fabs(rho[i] - rho_ref);
-        double dbar[6], rho_tilde, r_new[6];
-        int n_aps = or_pst_update(Nl - 1, rho + 1, delta + 6, rho_ref, r, beta, eps, dbar, &rho_tilde, r_new);
-        double s_new[7];
-        if (n_aps > 0) {
-            or_compose_offset(c, dbar, flags, s_new);
-            empty_run = 0;
-        } else {
-            memcpy(s_new, c, sizeof s_new);
-            ++empty_run;
-        }
-        rho_carry = rho_tilde;
-        memcpy(c, s_new, sizeof c);
-        memcpy(r, r_new, sizeof r);
-        if (k == 1)
-            memcpy(r1_out, r, sizeof r);
-        double step = 0.0;
-        for (int d = 0; d < 6; ++d)
-            step = fmax(step, fabs(dbar[d]));
-        int stop = 0;
-        if (empty_run >= 2)
-            stop = 1;
-        else if (n_aps > 0 && step < stop_eps)
-            stop = 2;
-        else if (k == k_max)
-            stop = 3;
-        if (tr) {
-            tr[0] = k;
-            tr[1] = nO;
-            tr[2] = n_aps;
-            tr[3] = rho_ref;
-            tr[4] = rho_tilde;
-            tr[5] = rho_max;
-            tr[6] = argmax;
-            for (int a = 0; a < 7; ++a)
-                tr[7 + a] = c[a];
-            for (int d = 0; d < 6; ++d) {
-                tr[14 + d] = r[d];
-                tr[20 + d] = dbar[d];
-            }
-            tr[26] = min_gap;
-            tr[27] = min_margin;
-            tr[28] = stop;
-            tr[29] = rho_2nd;
-            tr[30] = l;
-            tr[31] = Nl;
-        }
-        if (stop)
-            break;
-    }
-    if (k > k_max)
-        k = k_max;
-    memcpy(pose_out, c, sizeof c);
-    if (k == 1 && status == OR_ERR_EMPTY)
-        memcpy(r1_out, r0, sizeof r);
-    *iters_out = k;
-    free(mask);
-    free(margin);
-    free(rho);
-    free(delta);
-    return status;
 }

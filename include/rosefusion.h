@@ -67,6 +67,7 @@ typedef struct {
 #define RF_L1 32             /* sum |psi| instead of psi^2                               */
 #define RF_RIGHT_MULT 64     /* particle offset applied in the camera frame              */
 #define RF_CELL_MARGIN 128   /* O_k: re-projection inside frame t-1 by one cell footprint */
+#define RF_APS_WITH_CENTRE 256 /* the centre particle (s*_{k-1} itself) may join the APS */
 #define RF_DEFAULT_FLAGS (RF_OVERLAP | RF_NORMALIZE | RF_COMPENSATED | RF_CELL_MARGIN)
 
 /* Parameters of Algorithm 1; the defaults of the paper are tau = 1 (Sec. 3.2),
@@ -92,6 +93,9 @@ typedef struct {
     int stop;       /* 0 running, 1 empty twice, 2 small step, 3 k_max, 4 empty overlap */
     int level;      /* multi-resolution level used by this iteration          */
     int n_particles;/* particles scored (the level's prefix of the template)  */
+    int corner;     /* Sec. 4 "PST update" corner case taken: 0 none, 1 no TSDF
+                       sample for any particle (rho = 0.5, v = 1, r_hat = 0.5 + eps,
+                       s* kept), 2 empty APS (r_hat = 2 (1 - rho) / sqrt(6) + eps) */
 } rf_iter_stats;
 
 typedef struct {
@@ -234,15 +238,17 @@ rf_status fitness_eval(rf_volume v, const float *points_dev, int m, const float 
  * paper has no counterpart; this is a library service).  fitness_eval grows a
  * scratch buffer with cudaMalloc the first time a size needs it, and that call
  * synchronises the device and allocates.  Callers that cannot do either --
- * code inside CUDA stream capture, real-time loops that must never block on
- * the allocator, plug-in hosts that own a fixed memory budget -- use this
- * entry point instead.  Arguments, layouts and results are those of
+ * real-time loops that must never stall on a device-wide synchronisation or
+ * on the allocator, plug-in hosts that own a fixed memory budget and forbid
+ * their plug-ins to allocate -- use this entry point instead.  Arguments,
+ * layouts and results are those of
  * fitness_eval; the caller still provides every input and output buffer.
  *   Scratch: the per-chunk partial sums live in a 32 MiB static device array
  *   inside the library, which every GPU that loads the library holds until
  *   the process exits.  Sizes with ceil(m / 256) * n * 12 bytes above 32 MiB
- *   are rejected with RF_ERR_ARG (for example n = 20,000 allows m up to
- *   35,840 points).
+ *   are rejected with RF_ERR_ARG: n particles allow up to
+ *   floor(32 MiB / (12 n)) * 256 points (n = 20,000: 139 chunks, m up to
+ *   35,584).
  *   Set-up: the first call on each device (with that device current) looks
  *   up the array's device address with cudaGetSymbolAddress and caches it;
  *   make that first call before any stream capture.

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "librosefusion.so")
 RF_OK, RF_ERR_ARG, RF_ERR_CUDA, RF_ERR_TIMEOUT, RF_ERR_EMPTY, RF_ERR_NOMEM = 0, -1, -2, -3, -4, -5
 RF_OVERLAP, RF_NORMALIZE, RF_COMPENSATED, RF_NEAREST, RF_RHO_REF_CENTER, RF_L1, RF_RIGHT_MULT = 1, 2, 4, 8, 16, 32, 64
 RF_CELL_MARGIN = 128
+RF_APS_WITH_CENTRE = 256
 RF_DEFAULT_FLAGS = RF_OVERLAP | RF_NORMALIZE | RF_COMPENSATED | RF_CELL_MARGIN
 RF_MAX_ITERS = 64
 DTYPES = {"f32": 0, "f16": 1, "i16": 2}
@@ -51,7 +52,7 @@ class rf_iter_stats(ctypes.Structure):
                 ("rho_ref", ctypes.c_float), ("rho_tilde", ctypes.c_float), ("rho_max", ctypes.c_float),
                 ("rho_second", ctypes.c_float), ("pose", ctypes.c_float * 7), ("scale", ctypes.c_float * 6),
                 ("offset", ctypes.c_float * 6), ("stop", ctypes.c_int), ("level", ctypes.c_int),
-                ("n_particles", ctypes.c_int)]
+                ("n_particles", ctypes.c_int), ("corner", ctypes.c_int)]
 
 
 class rf_launch_config(ctypes.Structure):
@@ -97,7 +98,7 @@ EXPORTS = ["rf_last_error", "rf_version", "pst_create", "rf_volume_create", "rf_
            "rf_mlp_destroy", "rf_mlp_set_params", "rf_mlp_get_params", "rf_mlp_forward", "rf_mlp_gradient",
            "rf_mlp_train_step", "rf_mlp_status", "rf_proposal_features", "rf_proposal_target",
            "rf_proposal_default_params", "rf_proposal_apply", "rf_learned_create", "rf_learned_destroy",
-           "rf_learned_start", "rf_learned_step"]
+           "rf_learned_start", "rf_learned_step", "rf_l2_gather_probe", "rf_volume_counters"]
 
 
 def _load():
@@ -166,6 +167,8 @@ def _load():
         "rf_learned_destroy": (None, [P]),
         "rf_learned_start": (i, [P, P, i, ctypes.POINTER(rf_intrinsics), ctypes.POINTER(rf_pose), P]),
         "rf_learned_step": (i, [P, P, i, ctypes.POINTER(rf_intrinsics), i, ctypes.POINTER(rf_pose), P, P, P]),
+        "rf_l2_gather_probe": (i, [P, ctypes.c_size_t, i, i, P, P]),
+        "rf_volume_counters": (i, [P, ctypes.POINTER(ctypes.c_longlong), i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -229,7 +232,7 @@ def stats_dict(s: rf_frame_stats) -> dict:
         rows.append(dict(k=r.k, n_overlap=r.n_overlap, n_aps=r.n_aps, argmax=r.argmax, rho_ref=r.rho_ref,
                          rho_tilde=r.rho_tilde, rho_max=r.rho_max, rho_second=r.rho_second, pose=list(r.pose),
                          scale=list(r.scale), offset=list(r.offset), stop=r.stop, level=r.level,
-                         n_particles=r.n_particles))
+                         n_particles=r.n_particles, corner=r.corner))
     return dict(iters=s.iters, status=s.status, n_points=s.n_points, lookups=s.lookups, r1=list(s.r1), it=rows)
 
 
@@ -290,6 +293,12 @@ class Volume:
 
     def reset(self, stream=None):
         _check(lib.rf_volume_reset(self.handle, _stream(stream)))
+
+    def counters(self, reset=False):
+        """rf_volume_counters: dict(voxels_updated, bricks_visited, bricks_repacked)."""
+        out = (ctypes.c_longlong * 3)()
+        _check(lib.rf_volume_counters(self.handle, out, int(bool(reset))))
+        return dict(voxels_updated=out[0], bricks_visited=out[1], bricks_repacked=out[2])
 
     def upload(self, codes: np.ndarray, weights: np.ndarray | None = None):
         """codes: storage codes, shape (dz, dy, dx) or flat x-fastest."""
@@ -759,3 +768,10 @@ class Learned:
         if status < 0 and status != RF_ERR_EMPTY:
             _check(status)
         return (pose_array(out) if out is not None else None), status
+
+
+def rf_l2_gather_probe(buf, loads_per_thread, ctas_per_sm, sink, stream=None):
+    """One launch of the L2 gather microbenchmark over the CUDA tensor `buf`; sink:
+    CUDA uint32/int32 tensor of ctas_per_sm x SMs x 256 entries."""
+    _check(lib.rf_l2_gather_probe(_dptr(buf), buf.numel() * buf.element_size(), int(loads_per_thread),
+                                  int(ctas_per_sm), _dptr(sink), _stream(stream)))

@@ -52,6 +52,9 @@ struct VolumeDesc {
     // every cell touching an unobserved voxel (invalid).  Lookups in constant
     // bricks skip the cell load.
     uint8_t *brick_class;
+    // fusion counters since the last read-out: [0] voxels updated, [1] bricks that
+    // passed the frustum test, [2] bricks whose cells were repacked
+    unsigned long long *counters;
     int cell_stride[3];// brick-layout strides of one brick step per axis (in records)
     int dim[3];
     int nb[3];

@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kern
     __shared__ double red_d[FIT_WARPS][8];
     __shared__ float red_f[FIT_WARPS][2];
     __shared__ int red_i[FIT_WARPS][2];
+    __shared__ long long red_v[FIT_WARPS];
     __shared__ int s_total_units;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -455,17 +456,20 @@ __global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kern
             }
             __syncthreads();
             const float rho_ref = st[p].rho_ref;
+            // particle 0 is the centre s*_{k-1} itself: an APS candidate only with RF_APS_WITH_CENTRE
+            const int first = (pd.flags & RF_APS_WITH_CENTRE) ? 0 : 1;
             double sw = 0.0, swr = 0.0, swd[6] = {0, 0, 0, 0, 0, 0};
             int naps = 0, amax = -1;
+            long long valid = 0;  // valid TSDF samples of all particles (first corner case of Sec. 4)
             float rmax = -1.f, r2 = -1.f;
             for (int i = b * blockDim.x + tid; i < st[p].n_lvl; i += G * blockDim.x) {
                 double S;
                 int nv;
                 particle_total(pd.part_S, pd.part_n, st[p].n_lvl, st[p].n_chunks, i, true, S, nv);
+                valid += nv;
                 const float rho = fitness_rho(S, st[p].nO, pd.tau, normalize);
                 merge_max(rmax, amax, r2, rho, i, -1.f);
-                // particle 0 is the centre s*_{k-1} itself: never a member of the APS
-                if (i > 0 && rho > rho_ref) {
+                if (i >= first && rho > rho_ref) {
                     const double wgt = (double)(rho - rho_ref);
                     ++naps;
                     sw += wgt;
@@ -482,6 +486,7 @@ __global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kern
                 for (int d = 0; d < 6; ++d)
                     swd[d] += __shfl_xor_sync(0xffffffffu, swd[d], o);
                 naps += __shfl_xor_sync(0xffffffffu, naps, o);
+                valid += __shfl_xor_sync(0xffffffffu, valid, o);
                 const float om = __shfl_xor_sync(0xffffffffu, rmax, o);
                 const int oa = __shfl_xor_sync(0xffffffffu, amax, o);
                 const float o2 = __shfl_xor_sync(0xffffffffu, r2, o);
@@ -496,16 +501,19 @@ __global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kern
                 red_i[w][1] = amax;
                 red_f[w][0] = rmax;
                 red_f[w][1] = r2;
+                red_v[w] = valid;
             }
             __syncthreads();
             if (tid == 0) {
                 double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                 int na = 0, am = -1;
+                long long nv_all = 0;
                 float rm = -1.f, rs = -1.f;
                 for (int q = 0; q < FIT_WARPS; ++q) {
                     for (int e = 0; e < 8; ++e)
                         acc[e] += red_d[q][e];
                     na += red_i[q][0];
+                    nv_all += red_v[q];
                     merge_max(rm, am, rs, red_f[q][0], red_i[q][1], red_f[q][1]);
                 }
                 double *out = P.aps + ((size_t)b * MAX_BATCH + p) * APW;
@@ -515,6 +523,7 @@ __global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kern
                 out[9] = (double)rm;
                 out[10] = (double)am;
                 out[11] = (double)rs;
+                out[12] = (double)nv_all;  // exact: far below 2^53
             }
             __syncthreads();
         }
@@ -527,7 +536,7 @@ __global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kern
             const ProblemDesc &pd = P.prob[p];
             PState &s = st[p];
             double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            double na = 0.0;
+            double na = 0.0, nvalid = 0.0;
             float rm = -1.f, rs = -1.f;
             int am = -1;
             for (int q = lane; q < G; q += 32) {
@@ -535,24 +544,37 @@ __global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kern
                 for (int e = 0; e < 8; ++e)
                     acc[e] += __ldcg(&in[e]);
                 na += __ldcg(&in[8]);
+                nvalid += __ldcg(&in[12]);
                 merge_max(rm, am, rs, (float)__ldcg(&in[9]), (int)__ldcg(&in[10]), (float)__ldcg(&in[11]));
             }
             for (int o = 16; o > 0; o >>= 1) {
                 for (int e = 0; e < 8; ++e)
                     acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
                 na += __shfl_xor_sync(0xffffffffu, na, o);
+                nvalid += __shfl_xor_sync(0xffffffffu, nvalid, o);
                 const float om = __shfl_xor_sync(0xffffffffu, rm, o);
                 const int oa = __shfl_xor_sync(0xffffffffu, am, o);
                 const float o2 = __shfl_xor_sync(0xffffffffu, rs, o);
                 merge_max(rm, am, rs, om, oa, o2);
             }
             if (lane == 0) {
-                const int n_aps = (int)na;
+                // first corner case of Sec. 4: no particle found a single TSDF sample, so the
+                // likelihood cannot be evaluated: rho = 0.5, v = 1, r_hat = 0.5 v + eps, s* kept
+                const int corner = nvalid == 0.0 ? 1 : (na == 0.0 ? 2 : 0);
+                const int n_aps = corner == 1 ? 0 : (int)na;
                 const float rho_ref = s.rho_ref;
                 float dbar[6], rhat[6];
                 float rho_t;
                 Pose s_new;
-                if (n_aps > 0) {
+                if (corner == 1) {
+                    rho_t = 0.5f;
+                    for (int d = 0; d < 6; ++d) {
+                        dbar[d] = 0.f;
+                        rhat[d] = (float)(0.5 + (double)pd.eps);
+                    }
+                    s_new = s.c;
+                    s.empty_run += 1;
+                } else if (n_aps > 0) {
                     double nv2 = 0.0, db[6];
                     for (int d = 0; d < 6; ++d) {
                         db[d] = acc[2 + d] / acc[0];
@@ -616,6 +638,7 @@ __global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kern
                     row.stop = stop;
                     row.level = s.level;
                     row.n_particles = s.n_lvl;
+                    row.corner = corner;
                 }
             }
         }

@@ -11,6 +11,7 @@
 #include <string>
 
 #include "common.cuh"
+#include "rf_measure.h"
 
 namespace rf {
 
@@ -235,8 +236,13 @@ __global__ void __launch_bounds__(512) integrate_kernel(VolumeDesc V, const floa
         } while (false);
         // mark the brick so that its packed cells (and those of the cells reaching
         // into it from the lower neighbours) are rebuilt
-        if (__syncthreads_or(updated) && l == 0)
-            V.dirty[b] = 1;
+        const int n_updated = __syncthreads_count(updated);
+        if (l == 0) {
+            if (n_updated)
+                V.dirty[b] = 1;
+            atomicAdd(&V.counters[0], (unsigned long long)n_updated);
+            atomicAdd(&V.counters[1], 1ull);
+        }
     }
 }
 
@@ -330,6 +336,8 @@ __global__ void __launch_bounds__(512) pack_cells_kernel(VolumeDesc V, int all, 
             continue;  // uniform across the CTA (also every brick past the end)
         const int b = blockIdx.x * FUSE_BRICKS_PER_CTA + j;
         pack_brick<DT>(V, b, b % V.nb[0], (b / V.nb[0]) % V.nb[1], b / (V.nb[0] * V.nb[1]), l);
+        if (l == 0)
+            atomicAdd(&V.counters[2], 1ull);
     }
 }
 
@@ -448,12 +456,17 @@ rf_status rf_volume_create(int dx, int dy, int dz, float voxel, float trunc, con
         e = cudaMalloc(&d.dirty, v->n_vox / BRICK_VOX);
     if (e == cudaSuccess)
         e = cudaMalloc(&d.brick_class, v->n_vox / BRICK_VOX);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&d.counters, 3 * sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = cudaMemset(d.counters, 0, 3 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         cudaFree(d.values);
         cudaFree(d.weights);
         cudaFree(d.cells);
         cudaFree(d.dirty);
         cudaFree(d.brick_class);
+        cudaFree(d.counters);
         delete v;
         return cuda_fail(e, "cudaMalloc(volume)");
     }
@@ -476,8 +489,22 @@ void rf_volume_destroy(rf_volume v)
     cudaFree(v->d.cells);
     cudaFree(v->d.dirty);
     cudaFree(v->d.brick_class);
+    cudaFree(v->d.counters);
     cudaFree(v->scratch);
     delete v;
+}
+
+rf_status rf_volume_counters(rf_volume v, long long out_host[3], int reset)
+{
+    RF_CHECK_ARG(v && out_host, "null pointer");
+    unsigned long long h[3];
+    RF_CUDA(cudaDeviceSynchronize());
+    RF_CUDA(cudaMemcpy(h, v->d.counters, sizeof h, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 3; ++i)
+        out_host[i] = (long long)h[i];
+    if (reset)
+        RF_CUDA(cudaMemset(v->d.counters, 0, sizeof h));
+    return RF_OK;
 }
 
 rf_status rf_volume_reset(rf_volume v, void *stream)

@@ -3,11 +3,11 @@ centre c_0 apart from the previous pose, caller-held axis lengths, iteration
 cap, run flag) against the FP64 oracle's Algorithm 1 with the same
 initialisation, and the learned driver (rf_learned_step): its proposal, its
 short PFO run and its fallback rule.  Trace parity bar as in
-test_gpu_tracker.py."""
+test_gpu_tracker.py (every iteration replayed)."""
 import numpy as np
 import pytest
 
-from gpu_common import analytic_volume_codes, compare_traces, oracle_volume, pose_f32
+from gpu_common import analytic_volume_codes, oracle_volume, pose_f32, replay_trace
 from oracle import mlp
 from paper_2105_05600_gb300 import synth
 
@@ -74,17 +74,12 @@ def test_ex_async_with_a_separate_centre(oracle, nat, tiny):
     gst = nat.stats_dict(nat.stats_from_device(st))
     assert gst["status"] == 0 and 1 <= gst["iters"] <= k_max
     pts = oracle.unproject(tiny["depths"][1], K, cfg["stride"])
-    res = tiny["ov"].pfo_frame(pts, tiny["depths"][0], K, prev, c0, r0.astype(np.float64), oracle.pst_uniform(n, 1),
-                               oracle_params(oracle, k_max, flags))
-    assert res["status"] == 0
-    strict = compare_traces(gst, res["trace"])
-    assert strict >= 1
-    if strict == len(res["trace"]) == gst["iters"]:
-        got = out.cpu().numpy().astype(np.float64)
-        if np.dot(got[:4], res["pose"][:4]) < 0:
-            got[:4] = -got[:4]
-        np.testing.assert_allclose(got, res["pose"], atol=2e-4)
-        np.testing.assert_allclose(t_r.cpu().numpy(), res["r1"], rtol=2e-3, atol=2e-6)
+    res = replay_trace(oracle, tiny["ov"], gst, [(pts, n)], tiny["depths"][0], K, prev, c0, r0.astype(np.float64),
+                       oracle.pst_uniform(n, 1), oracle_params(oracle, k_max, flags))
+    assert res["loose"] <= max(1, res["rows"] // 4), res
+    # outputs: the last row's pose, r_1 = the first row's axis lengths
+    np.testing.assert_array_equal(out.cpu().numpy(), np.float32(gst["it"][-1]["pose"]))
+    np.testing.assert_array_equal(t_r.cpu().numpy(), np.float32(gst["it"][0]["scale"]))
     # the tracker's own r_0 buffer was not touched
     np.testing.assert_allclose(tr.get_scale(), np.ones(6))
 

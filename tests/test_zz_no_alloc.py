@@ -1,6 +1,6 @@
 """fitness_eval_noalloc: the fitness entry point for callers that cannot let the
-library allocate device memory (stream capture, real-time loops, fixed memory
-budgets).  It must give the same per-particle fitness as fitness_eval (within
+library allocate device memory (real-time loops that must not stall on the
+allocator's device-wide synchronisation, hosts with a fixed memory budget).  It must give the same per-particle fitness as fitness_eval (within
 the rel 1e-4 bar of the fitness parity tests) on two calls in a row, reject
 sizes beyond its 32 MiB static scratch with an error, and work both in a fresh
 process and after every other test.  This file is collected last on purpose."""

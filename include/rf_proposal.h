@@ -100,6 +100,32 @@ rf_status rf_mlp_gradient(rf_mlp m, const uint16_t *x_all_dev, const float *y_al
  * with learning rate lr on the FP32 parameters. */
 rf_status rf_mlp_train_step(rf_mlp m, const uint16_t *x_all_dev, const float *y_all_dev, const int *idx_dev, int n_all,
                             int batch, float lr, float *loss_dev, void *stream);
+/*
+ * rf_mlp_evaluate -- the network over dataset rows (forward passes of at most
+ * max_batch rows at a time) and the quantities its training selects and
+ * calibrates with.  Per row: mu = x[768..773] + o[0..5], s = clamp(o[6..11],
+ * -6, 6), e = y - mu.  The rows are idx_dev[0..n_rows) of the data set (rows
+ * 0..n_rows-1 when idx_dev is NULL); a row outside [0, n_all) sets RF_ERR_ARG in
+ * rf_mlp_status and is skipped.
+ *   mu_dev     device float[n_rows * 6] or NULL: mu of every row
+ *   stats_dev  device double[RF_MLP_EVAL_STATS] or NULL, means over the rows:
+ *              [0] sum_d e_d^2 (the squared offset error), [1 + d] e_d^2
+ *              exp(-2 s_d) (the calibration moments), [7 + d] y_d^2 (the error
+ *              of the zero offset, i.e. of the Sec. 4 initialisation, per axis)
+ * The row sums run in FP64 in a fixed order.  Asynchronous.
+ */
+#define RF_MLP_EVAL_STATS 13
+rf_status rf_mlp_evaluate(rf_mlp m, const uint16_t *x_all_dev, const float *y_all_dev, const int *idx_dev,
+                          int n_all, int n_rows, float *mu_dev, double *stats_dev, void *stream);
+/*
+ * rf_mlp_calibrate_scale -- per-axis calibration of the log-scale head on dataset
+ * rows (same row selection as rf_mlp_evaluate): with k_d^2 the mean of e_d^2
+ * exp(-2 s_d) over the rows, log k_d is added to the output bias of s_d, so that
+ * the predicted variances exp(2 s_d) match the rows' squared errors.  k_host
+ * (host float[6]) receives k.  Synchronous.
+ */
+rf_status rf_mlp_calibrate_scale(rf_mlp m, const uint16_t *x_all_dev, const float *y_all_dev, const int *idx_dev,
+                                 int n_all, int n_rows, float k_host[6], void *stream);
 /* Device status of the network's kernels since the last call (bounded waits in
  * the tensor-core products report RF_ERR_TIMEOUT); resets it.  Synchronous. */
 rf_status rf_mlp_status(rf_mlp m);
@@ -131,6 +157,11 @@ typedef struct {
                         Sec. 4 (and the fallback rule did not fire), PFO resumes
                         from its s* and axis lengths for up to k_fallback more
                         iterations; 0: no second run in that case */
+    int stuck;       /* a learned run whose every iteration had an empty APS never
+                        left c_0 (its result is the proposal itself): 0 keep it,
+                        1 (default) resume PFO from c_0 with the carried r_1 of the
+                        Sec. 4 initialisation for up to k_fallback iterations,
+                        2 plain restart from s*_{t-1} */
 } rf_proposal_params;
 
 /* Fills *p with the defaults above. */
@@ -154,17 +185,19 @@ rf_status rf_proposal_apply(const float *out_dev, const uint16_t *x_dev, const f
  *   proposal (c_0, r_0) -> PFO with at most k_learned iterations from c_0
  *   (pfo_track_frame_ex_async; the overlap set still uses s*_{t-1}) -> if the
  *   fallback rule fires, plain PFO from s*_{t-1} with the carried r_1 and
- *   k_fallback iterations; else, with `resume`, if the learned run stopped at
- *   k_learned unconverged, PFO continues from its s* and axis lengths for up
- *   to k_fallback iterations; the result with the higher final rho_tilde is
- *   kept -> fusion (tsdf_integrate) of D_t at the kept pose.
+ *   k_fallback iterations; else if the run never left c_0, the `stuck` rule;
+ *   else, with `resume`, if the learned run stopped at k_learned unconverged,
+ *   PFO continues from its s* and axis lengths for up to k_fallback
+ *   iterations; the result with the higher final rho_tilde is kept -> fusion
+ *   (tsdf_integrate) of D_t at the kept pose.
  * Frames are at most max_width x max_height.  The tracker and network must not
  * be used by other calls while a step runs.
  */
 typedef struct rf_learned_s *rf_learned;
 typedef struct {
     int status;          /* final status of the frame (0 = OK) */
-    int used_fallback;   /* second run: 0 none, 1 plain restart, 2 resumed */
+    int used_fallback;   /* second run: 0 none, 1 plain restart, 2 resumed, 3 resumed
+                            from a proposal the learned run never left */
     int chose_fallback;  /* its result was kept */
     int iters_learned;
     int iters_fallback;

@@ -348,6 +348,35 @@ rf_status pfo_track_frame(rf_tracker tr, const float *depth_dev, const float *pr
 /* Status written by the last finished frame (synchronises the tracker's state copy). */
 rf_status rf_tracker_last_status(rf_tracker tr);
 
+/*
+ * Launch configuration of the persistent PFO kernel (a tracker's own frames, or a
+ * batch).  The work split and the lookup group regroup the FP32 partial sums of
+ * the fitness, so different configurations agree to rounding, not bit for bit;
+ * one configuration always gives the same results.
+ */
+typedef struct {
+    int ctas_per_sm;  /* resident CTAs of 256 threads per SM, 0 = as many as fit      */
+    int work_warps;   /* warp count the work split targets (about 16 units per warp):
+                         1 .. 7296; the default 3648                                   */
+    int group;        /* lookups per lane whose loads are in flight together: 4, 6 or 8
+                         (0 = 6); nearest-voxel sampling ignores it                     */
+    float ms;         /* measured PFO kernel time of the chosen configuration (autotune) */
+} rf_launch_config;
+/* Set / read the configuration of a tracker's own frames (default {0, 3648, 6}). */
+rf_status rf_tracker_set_config(rf_tracker tr, const rf_launch_config *cfg);
+rf_status rf_tracker_get_config(rf_tracker tr, rf_launch_config *cfg);
+/*
+ * rf_tracker_autotune -- times the persistent kernel on one frame
+ * (pfo_track_frame_async's inputs) for candidate configurations -- first CTAs
+ * per SM x work warps {1824, 3648, 7296} with groups of 6, then groups of 4
+ * and 8 at the best of those -- keeps the fastest as the tracker's
+ * configuration and returns it (ms = its kernel time).  The tracker's r_0 is
+ * restored; nothing else of the tracker's state changes.  Synchronous.
+ */
+rf_status rf_tracker_autotune(rf_tracker tr, const float *depth_dev, const float *prev_depth_dev,
+                              const rf_intrinsics *K, const float *prev_pose_dev, rf_launch_config *chosen,
+                              void *stream);
+
 /* ------------------------------------------------------------ sequence --- */
 /*
  * Sequence mode: the tracker keeps the previous depth frame and pose on the
@@ -388,19 +417,15 @@ rf_status rf_sequence_step(rf_tracker tr, const float *depth, int depth_on_host,
  *                        stream; the graph is launched on `stream`)
  *   rf_batch_pose_dev    device float[7]: the pose of sequence i in slot parity
  *   rf_batch_autotune    times the PFO kernel of the frames currently in slot
- *                        `parity` for each candidate launch shape (CTAs per SM)
- *                        and work granularity, keeps the fastest and returns
- *                        its time (ms); inputs and tracker state are restored,
- *                        the volumes are not touched
+ *                        `parity` for the candidate configurations of
+ *                        rf_tracker_autotune (CTAs per SM, work warps, lookup
+ *                        group), keeps the fastest and returns it (ms); inputs
+ *                        and tracker state are restored, the volumes are not
+ *                        touched
  * Asynchronous except rf_batch_create / rf_batch_autotune.
  */
 #define RF_MAX_BATCH 16
 typedef struct rf_batch_s *rf_batch;
-typedef struct {
-    int ctas_per_sm;  /* resident CTAs of 256 threads per SM                            */
-    int work_warps;   /* warp count the work split targets (units of ~16 per warp)      */
-    float ms;         /* measured PFO kernel time of the chosen configuration (autotune) */
-} rf_launch_config;
 rf_status rf_batch_create(const rf_tracker *trackers, int n, const rf_intrinsics *K, rf_batch *out);
 void rf_batch_destroy(rf_batch b);
 rf_status rf_batch_depth_slot(rf_batch b, int i, int parity, float **depth_dev);

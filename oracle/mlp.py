@@ -205,6 +205,31 @@ def velocity(acts):
     return acts[0][:, N_RES:D_IN]
 
 
+def evaluate(theta, X, Y, round_bf16=True):
+    """The quantities the training selects and calibrates with, over the rows of X
+    (the network's output O, mu = previous offset + correction, s = clamp(O[:,
+    6:12], -6, 6), e = Y - mu): returns (mu, stats) with stats the means over the
+    rows of [sum_d e_d^2, e_d^2 exp(-2 s_d) (d = 0..5), y_d^2 (d = 0..5)]."""
+    O, acts = forward(theta, X, round_bf16)
+    mu = mean_offset(O, velocity(acts))
+    s = np.clip(O[:, 6:12], -S_CLAMP, S_CLAMP)
+    e = np.asarray(Y, np.float64) - mu
+    stats = np.concatenate([[np.mean(np.sum(e * e, axis=1))], np.mean(e * e * np.exp(-2.0 * s), axis=0),
+                            np.mean(np.asarray(Y, np.float64) ** 2, axis=0)])
+    return mu, stats
+
+
+def calibrate_scale(theta, X, Y, round_bf16=True):
+    """Per-axis calibration of the log-scale head: k_d^2 = mean over the rows of
+    e_d^2 exp(-2 s_d) (evaluate's stats[1 + d]); log k_d is added to the output
+    bias of s_d.  Returns (new theta, k)."""
+    _, stats = evaluate(theta, X, Y, round_bf16)
+    k = np.sqrt(np.maximum(stats[1:7], 1e-12))
+    out = np.array(theta, np.float64, copy=True)
+    unflatten(out)[7][6:12] += np.log(k)
+    return out, k
+
+
 def loss(theta, X, Y, round_bf16=False):
     O, acts = forward(theta, X, round_bf16)
     return loss_and_grad_out(O, Y, velocity(acts))[0]

@@ -56,7 +56,8 @@ class rf_iter_stats(ctypes.Structure):
 
 
 class rf_launch_config(ctypes.Structure):
-    _fields_ = [("ctas_per_sm", ctypes.c_int), ("work_warps", ctypes.c_int), ("ms", ctypes.c_float)]
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("work_warps", ctypes.c_int), ("group", ctypes.c_int),
+                ("ms", ctypes.c_float)]
 
 
 class rf_frame_stats(ctypes.Structure):
@@ -73,7 +74,7 @@ class rf_track_options(ctypes.Structure):
 class rf_proposal_params(ctypes.Structure):
     _fields_ = [("k_learned", ctypes.c_int), ("k_fallback", ctypes.c_int), ("kappa", ctypes.c_float),
                 ("theta", ctypes.c_float), ("r_min", ctypes.c_float * 6), ("r_max", ctypes.c_float * 6),
-                ("resume", ctypes.c_int)]
+                ("resume", ctypes.c_int), ("stuck", ctypes.c_int)]
 
 
 class rf_learned_stats(ctypes.Structure):
@@ -85,6 +86,7 @@ class rf_learned_stats(ctypes.Structure):
 
 RF_MLP_IN, RF_MLP_IN_USED, RF_MLP_HIDDEN, RF_MLP_OUT, RF_MLP_OUT_USED = 832, 774, 256, 16, 12
 RF_MLP_MAX_BATCH, RF_MLP_MAX_TRAIN_BATCH = 4096, 1024
+RF_MLP_EVAL_STATS = 13
 
 EXPORTS = ["rf_last_error", "rf_version", "pst_create", "rf_volume_create", "rf_volume_destroy", "rf_volume_reset",
            "rf_volume_upload", "rf_volume_download", "rf_volume_info", "tsdf_integrate", "tsdf_integrate_dev",
@@ -98,7 +100,9 @@ EXPORTS = ["rf_last_error", "rf_version", "pst_create", "rf_volume_create", "rf_
            "rf_mlp_destroy", "rf_mlp_set_params", "rf_mlp_get_params", "rf_mlp_forward", "rf_mlp_gradient",
            "rf_mlp_train_step", "rf_mlp_status", "rf_proposal_features", "rf_proposal_target",
            "rf_proposal_default_params", "rf_proposal_apply", "rf_learned_create", "rf_learned_destroy",
-           "rf_learned_start", "rf_learned_step", "rf_l2_gather_probe", "rf_volume_counters"]
+           "rf_learned_start", "rf_learned_step", "rf_l2_gather_probe", "rf_volume_counters",
+           "rf_tracker_set_config", "rf_tracker_get_config", "rf_tracker_autotune", "rf_mlp_evaluate",
+           "rf_mlp_calibrate_scale"]
 
 
 def _load():
@@ -147,6 +151,9 @@ def _load():
         "rf_batch_step": (i, [P, i, i, P]),
         "rf_batch_autotune": (i, [P, i, ctypes.POINTER(rf_launch_config), P]),
         "rf_batch_set_config": (i, [P, ctypes.POINTER(rf_launch_config)]),
+        "rf_tracker_set_config": (i, [P, ctypes.POINTER(rf_launch_config)]),
+        "rf_tracker_get_config": (i, [P, ctypes.POINTER(rf_launch_config)]),
+        "rf_tracker_autotune": (i, [P, P, P, ctypes.POINTER(rf_intrinsics), P, ctypes.POINTER(rf_launch_config), P]),
         "rf_batch_stats_dev": (i, [P, ctypes.POINTER(P)]),
         "pfo_track_frame_ex_async": (i, [P, P, P, ctypes.POINTER(rf_intrinsics), P, P, P,
                                          ctypes.POINTER(rf_track_options), P]),
@@ -159,6 +166,8 @@ def _load():
         "rf_mlp_gradient": (i, [P, P, P, P, i, i, P, P, P, P]),
         "rf_mlp_train_step": (i, [P, P, P, P, i, i, f, P, P]),
         "rf_mlp_status": (i, [P]),
+        "rf_mlp_evaluate": (i, [P, P, P, P, i, i, P, P, P]),
+        "rf_mlp_calibrate_scale": (i, [P, P, P, P, i, i, ctypes.POINTER(ctypes.c_float), P]),
         "rf_proposal_features": (i, [P, P, ctypes.POINTER(rf_intrinsics), P, P, P, P]),
         "rf_proposal_target": (i, [P, P, P, P]),
         "rf_proposal_default_params": (None, [ctypes.POINTER(rf_proposal_params)]),
@@ -167,7 +176,7 @@ def _load():
         "rf_learned_destroy": (None, [P]),
         "rf_learned_start": (i, [P, P, i, ctypes.POINTER(rf_intrinsics), ctypes.POINTER(rf_pose), P]),
         "rf_learned_step": (i, [P, P, i, ctypes.POINTER(rf_intrinsics), i, ctypes.POINTER(rf_pose), P, P, P]),
-        "rf_l2_gather_probe": (i, [P, ctypes.c_size_t, i, i, P, P]),
+        "rf_l2_gather_probe": (i, [P, ctypes.c_size_t, i, i, i, P, P]),
         "rf_volume_counters": (i, [P, ctypes.POINTER(ctypes.c_longlong), i]),
     }
     for name, (res, args) in sig.items():
@@ -223,6 +232,10 @@ def pose_array(p: rf_pose) -> np.ndarray:
 
 def make_params(tau=1.0, beta=0.1, eps=1e-3, stop_eps=1e-6, k_max=20, flags=RF_DEFAULT_FLAGS, stride=1) -> rf_params:
     return rf_params(tau, beta, eps, stop_eps, int(k_max), int(flags), int(stride), 0)
+
+
+def config_dict(cfg: rf_launch_config) -> dict:
+    return dict(ctas_per_sm=cfg.ctas_per_sm, work_warps=cfg.work_warps, group=cfg.group, ms=cfg.ms)
 
 
 def stats_dict(s: rf_frame_stats) -> dict:
@@ -431,6 +444,26 @@ class Tracker:
         _check(lib.rf_tracker_set_params(self.handle, ctypes.byref(params)))
         self.params = params
 
+    def set_config(self, ctas_per_sm=0, work_warps=3648, group=0):
+        cfg = rf_launch_config(int(ctas_per_sm), int(work_warps), int(group), 0.0)
+        _check(lib.rf_tracker_set_config(self.handle, ctypes.byref(cfg)))
+
+    def get_config(self):
+        cfg = rf_launch_config()
+        _check(lib.rf_tracker_get_config(self.handle, ctypes.byref(cfg)))
+        return config_dict(cfg)
+
+    def autotune(self, depth, prev_depth, K: dict, prev_pose_dev, stream=None):
+        """rf_tracker_autotune on one frame; returns the chosen configuration."""
+        import torch
+
+        Ki = make_intrinsics(K)
+        cfg = rf_launch_config()
+        _check(lib.rf_tracker_autotune(self.handle, _dptr(depth, torch.float32), _dptr(prev_depth, torch.float32),
+                                       ctypes.byref(Ki), _dptr(prev_pose_dev, torch.float32), ctypes.byref(cfg),
+                                       _stream(stream)))
+        return config_dict(cfg)
+
     def last_status(self):
         return lib.rf_tracker_last_status(self.handle)
 
@@ -500,10 +533,10 @@ class Batch:
     def autotune(self, parity, stream=None):
         cfg = rf_launch_config()
         _check(lib.rf_batch_autotune(self.handle, int(parity), ctypes.byref(cfg), _stream(stream)))
-        return dict(ctas_per_sm=cfg.ctas_per_sm, work_warps=cfg.work_warps, ms=cfg.ms)
+        return config_dict(cfg)
 
-    def set_config(self, ctas_per_sm=0, work_warps=3648):
-        cfg = rf_launch_config(int(ctas_per_sm), int(work_warps), 0.0)
+    def set_config(self, ctas_per_sm=0, work_warps=3648, group=0):
+        cfg = rf_launch_config(int(ctas_per_sm), int(work_warps), int(group), 0.0)
         _check(lib.rf_batch_set_config(self.handle, ctypes.byref(cfg)))
 
 
@@ -668,6 +701,29 @@ class MLP:
                                      _dptr(idx, torch.int32), int(x_all.shape[0]), int(batch), float(lr),
                                      _dptr(loss_out, torch.float32), _stream(stream)))
 
+    def evaluate(self, x_all, y_all, idx=None, n_rows=None, mu_out=None, stream=None):
+        """rf_mlp_evaluate: (mu float32 (rows, 6) CUDA tensor, stats float64[13] CUDA
+        tensor) over rows idx (or the first n_rows)."""
+        import torch
+
+        rows = int(idx.shape[0]) if idx is not None else int(n_rows or x_all.shape[0])
+        mu = mu_out if mu_out is not None else torch.empty((rows, 6), dtype=torch.float32, device=x_all.device)
+        stats = torch.empty(RF_MLP_EVAL_STATS, dtype=torch.float64, device=x_all.device)
+        _check(lib.rf_mlp_evaluate(self.handle, _bf16_ptr(x_all), _dptr(y_all, torch.float32),
+                                   _dptr(idx, torch.int32), int(x_all.shape[0]), rows, _dptr(mu), _dptr(stats),
+                                   _stream(stream)))
+        return mu, stats
+
+    def calibrate_scale(self, x_all, y_all, idx=None, n_rows=None, stream=None):
+        """rf_mlp_calibrate_scale: adds log k to the log-scale output biases; returns k."""
+        import torch
+
+        rows = int(idx.shape[0]) if idx is not None else int(n_rows or x_all.shape[0])
+        k = (ctypes.c_float * 6)()
+        _check(lib.rf_mlp_calibrate_scale(self.handle, _bf16_ptr(x_all), _dptr(y_all, torch.float32),
+                                          _dptr(idx, torch.int32), int(x_all.shape[0]), rows, k, _stream(stream)))
+        return [float(v) for v in k]
+
     def status(self) -> int:
         return lib.rf_mlp_status(self.handle)
 
@@ -770,8 +826,9 @@ class Learned:
         return (pose_array(out) if out is not None else None), status
 
 
-def rf_l2_gather_probe(buf, loads_per_thread, ctas_per_sm, sink, stream=None):
-    """One launch of the L2 gather microbenchmark over the CUDA tensor `buf`; sink:
-    CUDA uint32/int32 tensor of ctas_per_sm x SMs x 256 entries."""
+def rf_l2_gather_probe(buf, loads_per_thread, ctas_per_sm, sink, mode=0, stream=None):
+    """One launch of the gather microbenchmark over the CUDA tensor `buf` (mode 0:
+    random 16-byte records, 1: random 128-byte lines); sink: CUDA uint32/int32
+    tensor of ctas_per_sm x SMs x 256 entries."""
     _check(lib.rf_l2_gather_probe(_dptr(buf), buf.numel() * buf.element_size(), int(loads_per_thread),
-                                  int(ctas_per_sm), _dptr(sink), _stream(stream)))
+                                  int(ctas_per_sm), int(mode), _dptr(sink), _stream(stream)))

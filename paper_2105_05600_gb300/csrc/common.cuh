@@ -276,6 +276,15 @@ template <> struct CellData<RF_F32> {
     float4 a, b;
 };
 
+// RF_CELL_CLASS = 1: lookups in constant bricks skip the record (class byte
+// first, then a predicated record load); 0: every lookup inside the volume loads
+// its own record, which packing writes for every brick, so both give the same
+// values -- the second trades L2 traffic for fewer instructions and one
+// dependent load less per lookup.
+#ifndef RF_CELL_CLASS
+#define RF_CELL_CLASS 1
+#endif
+
 __device__ __forceinline__ void cell_locate(const CellView &V, float gx, float gy, float gz, CellRef &c)
 {
     const int ix = floor_split(gx, c.fx), iy = floor_split(gy, c.fy), iz = floor_split(gz, c.fz);
@@ -284,7 +293,12 @@ __device__ __forceinline__ void cell_locate(const CellView &V, float gx, float g
     const unsigned brick =
         (unsigned)(ix >> 3) + (unsigned)V.nb0 * ((unsigned)(iy >> 3) + (unsigned)V.nb1 * (unsigned)(iz >> 3));
     c.rec = brick * (unsigned)BRICK_VOX + (unsigned)((ix & 7) | ((iy & 7) << 3) | ((iz & 7) << 6));
+#if RF_CELL_CLASS
     c.cls = inside ? (unsigned)__ldg(&V.cls[brick]) : (unsigned)CELLS_INVALID;
+#else
+    c.cls = inside ? (unsigned)CELLS_MIXED : (unsigned)CELLS_INVALID;
+    c.rec = inside ? c.rec : 0u;  // any record in bounds; cell_fetch invalidates it
+#endif
 }
 
 // The record of a constant brick is not loaded: the registers get a fill
@@ -299,6 +313,21 @@ __device__ __forceinline__ void ldg_v4_if(bool p, const void *ptr, uint32_t &x, 
 
 template <int DT> __device__ __forceinline__ void cell_fetch(const CellView &V, const CellRef &c, CellData<DT> &d)
 {
+#if !RF_CELL_CLASS
+    // unconditional load of the (in-bounds) record; outside the volume the first
+    // word is replaced by an invalid pattern (zero int16 codes, NaN halves/float)
+    const bool inside = c.cls == CELLS_MIXED;
+    if constexpr (DT == RF_F32) {
+        const float4 *cp = reinterpret_cast<const float4 *>(V.cells) + 2 * (size_t)c.rec;
+        d.a = __ldg(cp);
+        d.b = __ldg(cp + 1);
+        d.a.x = inside ? d.a.x : __int_as_float(0x7FC00000);
+    } else {
+        d.a = __ldg(reinterpret_cast<const uint4 *>(V.cells) + c.rec);
+        d.a.x = inside ? d.a.x : (DT == RF_I16 ? 0u : 0x7E007E00u);
+    }
+    return;
+#endif
     const bool mixed = c.cls == CELLS_MIXED, free_space = c.cls == CELLS_FREE;
     if constexpr (DT == RF_F32) {
         // +1.0f for free space, NaN (invalid) otherwise

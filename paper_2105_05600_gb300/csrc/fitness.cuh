@@ -30,7 +30,9 @@ constexpr int MAX_CTAS_PER_SM = 2048 / FIT_THREADS;  // bound for grid-sized scr
 #ifndef RF_PFO_MIN_BLOCKS
 #define RF_PFO_MIN_BLOCKS 2
 #endif
-// lookups whose loads are issued together in the trilinear loop
+// lookups whose loads are issued together in the trilinear loop (the default;
+// the persistent kernel is also built for groups of 4 and 8, picked by the
+// launch configuration)
 #ifndef RF_GROUP
 #define RF_GROUP 6
 #endif
@@ -103,13 +105,14 @@ struct FitParams {
     int l1, right_mult;
 };
 
-template <int DT, int MODE, bool L1>
+template <int DT, int MODE, bool L1, int G>
 __device__ __forceinline__ void fitness_points(const CellView &V, const float4 *spts, int cnt, const float R[9],
                                                float t0, float t1, float t2, float &sum, float &comp, int &nv);
 
 // Lane `lane` of a warp scores particle i over the points staged in `spts`
-// [0, cnt): S = sum psi^2 (|psi| with L1), psi = 1 for invalid samples.
-template <int DT, int MODE>
+// [0, cnt): S = sum psi^2 (|psi| with L1), psi = 1 for invalid samples; G
+// lookups have their loads in flight together.
+template <int DT, int MODE, int G = GROUP>
 __device__ __forceinline__ void fitness_lane(const VolumeDesc &V, const float4 *spts, int cnt, const FitParams &fp,
                                              int i, double &S_out, int &n_out)
 {
@@ -134,16 +137,16 @@ __device__ __forceinline__ void fitness_lane(const VolumeDesc &V, const float4 *
     int nv = 0;
     const CellView cv(V);
     if (fp.l1)
-        fitness_points<DT, MODE, true>(cv, spts, cnt, R, t0, t1, t2, sum, comp, nv);
+        fitness_points<DT, MODE, true, G>(cv, spts, cnt, R, t0, t1, t2, sum, comp, nv);
     else
-        fitness_points<DT, MODE, false>(cv, spts, cnt, R, t0, t1, t2, sum, comp, nv);
+        fitness_points<DT, MODE, false, G>(cv, spts, cnt, R, t0, t1, t2, sum, comp, nv);
     S_out = (double)sum + (double)comp;
     n_out = nv;
 }
 
 // The point loop of one lane: lookups of points [0, cnt) under the grid-space
 // pose (R, t), accumulated as psi^2 (|psi| with L1), psi = 1 when invalid.
-template <int DT, int MODE, bool L1>
+template <int DT, int MODE, bool L1, int G>
 __device__ __forceinline__ void fitness_points(const CellView &V, const float4 *spts, int cnt, const float R[9],
                                                float t0, float t1, float t2, float &sum, float &comp, int &nv)
 {
@@ -160,25 +163,25 @@ __device__ __forceinline__ void fitness_points(const CellView &V, const float4 *
         return L1 ? fabsf(psi) : psi * psi;
     };
     if (!Mode<MODE>::nearest) {
-        // groups of GROUP lookups: all class loads, then all cell loads, then the
+        // groups of G lookups: all class loads, then all cell loads, then the
         // arithmetic, so each group pays the load latency once; a plain FP32
-        // partial of <= GROUP terms in [0, 1] is then added with compensation
-        for (; j + GROUP <= cnt; j += GROUP) {
-            CellRef c[GROUP];
-            CellData<DT> d[GROUP];
+        // partial of <= G terms in [0, 1] is then added with compensation
+        for (; j + G <= cnt; j += G) {
+            CellRef c[G];
+            CellData<DT> d[G];
 #pragma unroll
-            for (int u = 0; u < GROUP; ++u) {
+            for (int u = 0; u < G; ++u) {
                 const float4 x = spts[j + u];
                 cell_locate(V, fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, t0))),
                             fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, t1))),
                             fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, t2))), c[u]);
             }
 #pragma unroll
-            for (int u = 0; u < GROUP; ++u)
+            for (int u = 0; u < G; ++u)
                 cell_fetch<DT>(V, c[u], d[u]);
             float grp = 0.f;
 #pragma unroll
-            for (int u = 0; u < GROUP; ++u) {
+            for (int u = 0; u < G; ++u) {
                 float psi;
                 const bool ok = cell_eval<DT>(c[u], d[u], psi);
                 grp += term(ok, psi);

@@ -180,17 +180,29 @@ struct LearnedState {
 // frame's; otherwise, with `resume`, a continuation from the learned run's state
 // (its s* and axis lengths) when that run used all k_learned iterations without
 // meeting a convergence criterion of Sec. 4 (stop reason k_max).
-__global__ void judge_kernel(LearnedState *S, float theta, int resume)
+__global__ void judge_kernel(LearnedState *S, float theta, int resume, int stuck)
 {
     const rf_frame_stats &l = S->st_l;
     const float rho = final_rho(&l);
     const int last = min(l.iters, RF_MAX_ITERS) - 1;
     const bool bad = l.status != 0 || l.iters == 0 || rho < theta * S->rho_prev;
     const bool open = last >= 0 && l.it[last].stop == 3;
-    const int mode = theta < 0.f ? 0 : bad ? 1 : (resume && open) ? 2 : 0;
+    bool moved = false;  // some iteration had a non-empty APS, i.e. s* left c_0
+    for (int k = 0; k <= last; ++k)
+        moved |= l.it[k].n_aps > 0;
+    // 1 plain restart, 2 resume of the learned run, 3 resume from c_0 with the carried r_1
+    int mode = 0;
+    if (theta >= 0.f) {
+        if (bad || (!moved && stuck == 2))
+            mode = 1;
+        else if (!moved && stuck == 1)
+            mode = 3;
+        else if (resume && open)
+            mode = 2;
+    }
     S->run_flag = mode;
     for (int a = 0; a < 7; ++a)
-        S->c_fb[a] = mode == 2 ? S->pose_l[a] : S->hist[1][a];
+        S->c_fb[a] = mode == 2 ? S->pose_l[a] : (mode == 3 ? S->c0[a] : S->hist[1][a]);
     for (int i = 0; i < 6; ++i)
         S->r_fb[i] = mode == 2 ? l.it[last].scale[i] : S->r_carry[i];
 }
@@ -260,6 +272,7 @@ rf_status check_params(const rf_proposal_params *p)
     RF_CHECK_ARG(p->k_fallback >= 1 && p->k_fallback <= RF_MAX_ITERS, "k_fallback outside [1, RF_MAX_ITERS]");
     RF_CHECK_ARG(p->kappa > 0.f, "kappa must be positive");
     RF_CHECK_ARG(p->resume == 0 || p->resume == 1, "resume must be 0 or 1");
+    RF_CHECK_ARG(p->stuck >= 0 && p->stuck <= 2, "stuck must be 0, 1 or 2");
     for (int i = 0; i < 6; ++i)
         RF_CHECK_ARG(p->r_min[i] > 0.f && p->r_max[i] >= p->r_min[i], "r_min / r_max");
     return RF_OK;
@@ -309,7 +322,7 @@ static rf_status learned_enqueue(rf_learned lp, const rf_intrinsics *K, rf_learn
     st = pfo_track_frame_ex_async(lp->tr, lp->depth_cur, lp->depth_prev, K, S->hist[1], S->pose_l, &S->st_l, &o, s);
     if (st != RF_OK)
         return st;
-    judge_kernel<<<1, 1, 0, s>>>(S, lp->p.theta, lp->p.resume);
+    judge_kernel<<<1, 1, 0, s>>>(S, lp->p.theta, lp->p.resume, lp->p.stuck);
     RF_CUDA(cudaGetLastError());
     memset(&o, 0, sizeof o);
     o.init_pose_dev = S->c_fb;
@@ -340,6 +353,7 @@ void rf_proposal_default_params(rf_proposal_params *p)
     p->kappa = 2.f;
     p->theta = 0.9f;
     p->resume = 1;
+    p->stuck = 1;
     for (int i = 0; i < 6; ++i) {
         p->r_min[i] = i < 3 ? 2e-3f : 4e-3f;
         p->r_max[i] = i < 3 ? 0.2f : 0.4f;

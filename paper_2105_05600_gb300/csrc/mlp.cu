@@ -29,6 +29,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -562,6 +563,70 @@ GemmEpi epi(int M, int N, int K, int mode, int *err, long long timeout_ns)
 }
 
 }  // namespace
+// The quantities training selects and calibrates the network with, over B rows
+// of a batch (outputs `out`, inputs `x`, targets `y`): mu = x_v + o_mu (x_v the
+// previous-offset inputs), s = clamp(o_s, -6, 6), e = y - mu, and per row
+// sum_d e_d^2, e_d^2 exp(-2 s_d), y_d^2 (13 values, FP64).  One CTA; thread t
+// takes rows t, t + blockDim, ...; the per-thread sums are combined by a fixed
+// shuffle tree and warp order, and thread 0 adds them to acc (the calls for the
+// successive batches of a data set run in stream order, so the total is fixed).
+constexpr int EVAL_STATS = 13;
+__global__ void eval_kernel(const float *out, const bf16 *x, const float *y, int B, int row0, float *mu_out,
+                            double *acc)
+{
+    __shared__ double red[EVAL_STATS][32];
+    double loc[EVAL_STATS];
+    for (int e = 0; e < EVAL_STATS; ++e)
+        loc[e] = 0.0;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        for (int d = 0; d < 6; ++d) {
+            const float mu = out[b * RF_MLP_OUT + d] +
+                             __bfloat162float(x[(size_t)b * RF_MLP_IN + RF_MLP_IN_USED - 6 + d]);
+            const float s = fminf(fmaxf(out[b * RF_MLP_OUT + 6 + d], -6.f), 6.f);
+            const double yd = (double)y[b * 6 + d];
+            const double e = yd - (double)mu;
+            loc[0] += e * e;
+            loc[1 + d] += e * e * exp(-2.0 * (double)s);
+            loc[7 + d] += yd * yd;
+            if (mu_out)
+                mu_out[(size_t)(row0 + b) * 6 + d] = mu;
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int e = 0; e < EVAL_STATS; ++e) {
+        double v = loc[e];
+        for (int o = 16; o > 0; o >>= 1)
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0)
+            red[e][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int e = 0; e < EVAL_STATS; ++e) {
+            double t = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
+                t += red[e][q];
+            acc[e] += t;
+        }
+}
+
+__global__ void eval_finish_kernel(const double *acc, int n_rows, double *stats)
+{
+    if (threadIdx.x < EVAL_STATS)
+        stats[threadIdx.x] = acc[threadIdx.x] / (double)n_rows;
+}
+
+// log k_d added to the output bias of the log-scale s_d, k_d^2 = stats[1 + d].
+__global__ void calibrate_kernel(const double *stats, float *bias_s, float *k_out)
+{
+    const int d = threadIdx.x;
+    if (d < 6) {
+        const double k = sqrt(fmax(stats[1 + d], 1e-12));
+        bias_s[d] += (float)log(k);
+        k_out[d] = (float)k;
+    }
+}
+
 }  // namespace rf
 
 using namespace rf;
@@ -577,6 +642,8 @@ struct rf_mlp_s {
     bf16 *d[3] = {}, *dt[3] = {};      // masked hidden gradients
     bf16 *g = nullptr, *gt = nullptr;  // output gradients
     float *out = nullptr, *y = nullptr, *loss = nullptr;
+    double *eval_acc = nullptr;  // rf_mlp_evaluate: running sums, then the means (2 x EVAL_STATS)
+    float *eval_k = nullptr;     // rf_mlp_calibrate_scale: k (6)
     int *err = nullptr;
     int step = 0;
     long long timeout_ns = 1000000000ll;
@@ -747,6 +814,10 @@ rf_status rf_mlp_create(int max_batch, rf_mlp *out)
         st = mlp_alloc(m, (void **)&m->loss, sizeof(float));
     if (st == RF_OK)
         st = mlp_alloc(m, (void **)&m->err, sizeof(int));
+    if (st == RF_OK)
+        st = mlp_alloc(m, (void **)&m->eval_acc, 2 * EVAL_STATS * sizeof(double));
+    if (st == RF_OK)
+        st = mlp_alloc(m, (void **)&m->eval_k, 6 * sizeof(float));
     if (st == RF_OK) {
         cudaError_t e = cudaMemset(m->theta, 0, P * sizeof(float));
         if (e == cudaSuccess)
@@ -847,6 +918,55 @@ rf_status rf_mlp_train_step(rf_mlp m, const uint16_t *x_all_dev, const float *y_
         return st;
     RF_CHECK_ARG(lr >= 0.f, "negative learning rate");
     return mlp_adam(m, 1, lr, (cudaStream_t)stream);
+}
+
+rf_status rf_mlp_evaluate(rf_mlp m, const uint16_t *x_all_dev, const float *y_all_dev, const int *idx_dev,
+                          int n_all, int n_rows, float *mu_dev, double *stats_dev, void *stream)
+{
+    RF_CHECK_ARG(m && x_all_dev && y_all_dev, "null pointer");
+    RF_CHECK_ARG(n_rows >= 1 && n_all >= 1 && (idx_dev || n_rows <= n_all), "dataset rows");
+    cudaStream_t s = (cudaStream_t)stream;
+    RF_CUDA(cudaMemsetAsync(m->eval_acc, 0, EVAL_STATS * sizeof(double), s));
+    const bf16 *x_all = reinterpret_cast<const bf16 *>(x_all_dev);
+    for (int r0 = 0; r0 < n_rows; r0 += m->max_batch) {
+        const int B = std::min(m->max_batch, n_rows - r0);
+        // rows idx[r0 ..] (or r0 ..) into the batch buffers; the transposed copy is unused here
+        if (idx_dev) {
+            gather_kernel<<<B, 256, 0, s>>>(x_all, y_all_dev, idx_dev + r0, n_all, B, m->x, m->xt, m->y, m->err);
+        } else {
+            gather_kernel<<<B, 256, 0, s>>>(x_all + (size_t)r0 * RF_MLP_IN, y_all_dev + (size_t)r0 * 6, nullptr,
+                                            n_all - r0, B, m->x, m->xt, m->y, m->err);
+        }
+        RF_CUDA(cudaGetLastError());
+        rf_status st = mlp_forward(m, m->x, B, m->out, 0, s);
+        if (st != RF_OK)
+            return st;
+        eval_kernel<<<1, 256, 0, s>>>(m->out, m->x, m->y, B, r0, mu_dev, m->eval_acc);
+        RF_CUDA(cudaGetLastError());
+    }
+    eval_finish_kernel<<<1, 32, 0, s>>>(m->eval_acc, n_rows, m->eval_acc + EVAL_STATS);
+    RF_CUDA(cudaGetLastError());
+    if (stats_dev)
+        RF_CUDA(cudaMemcpyAsync(stats_dev, m->eval_acc + EVAL_STATS, EVAL_STATS * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+    return RF_OK;
+}
+
+rf_status rf_mlp_calibrate_scale(rf_mlp m, const uint16_t *x_all_dev, const float *y_all_dev, const int *idx_dev,
+                                 int n_all, int n_rows, float k_host[6], void *stream)
+{
+    RF_CHECK_ARG(m && k_host, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    rf_status st = rf_mlp_evaluate(m, x_all_dev, y_all_dev, idx_dev, n_all, n_rows, nullptr, nullptr, stream);
+    if (st != RF_OK)
+        return st;
+    const LayerTable &L = m->L;
+    float *b4 = m->theta + L.w_off[3] + L.out[3] * L.in[3];
+    calibrate_kernel<<<1, 32, 0, s>>>(m->eval_acc + EVAL_STATS, b4 + 6, m->eval_k);
+    RF_CUDA(cudaGetLastError());
+    RF_CUDA(cudaMemcpyAsync(k_host, m->eval_k, 6 * sizeof(float), cudaMemcpyDeviceToHost, s));
+    RF_CUDA(cudaStreamSynchronize(s));
+    return RF_OK;
 }
 
 rf_status rf_mlp_status(rf_mlp m)

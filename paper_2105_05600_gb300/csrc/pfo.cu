@@ -20,649 +20,13 @@
 #include <algorithm>
 #include <vector>
 
-#include "fitness.cuh"
+#include "pfo_kernel.cuh"
 
 namespace rf {
 
-constexpr int MAX_BATCH = RF_MAX_BATCH;
-constexpr int MAX_LEVELS = RF_MAX_LEVELS;
-// The fitness split of a sequence is computed for this warp count (not for the
-// actual grid), so a sequence's results do not depend on the launch shape or on
-// the other sequences of a batch.
-constexpr int WORK_WARPS_DEFAULT = 3648;
-constexpr int WORK_WARPS_MAX = 7296;
-
-rf_status launch_integrate_dev(const VolumeDesc &V, const float *depth, const Intr &K, const float *pose_dev,
-                               const int *status_dev, cudaStream_t s);
-
-// ------------------------------------------------------------------ launch descriptors
-struct ProblemDesc {
-    VolumeDesc V;
-    Intr K;
-    const float *depth, *prev_depth;
-    const float *pst;  // template, structure of arrays, leading dimension n_tmpl
-    int n_tmpl;
-    int n_levels;
-    int lvl_n[MAX_LEVELS], lvl_stride[MAX_LEVELS], lvl_nw[MAX_LEVELS], lvl_m[MAX_LEVELS], lvl_off[MAX_LEVELS];
-    int m_all;  // points of all levels (concatenated in pts at lvl_off)
-    const float *prev_pose;
-    const float *init_pose;  // c_0 (NULL: prev_pose)
-    const int *run_flag;     // NULL, or skip the frame when *run_flag == 0 at launch
-    float *out_pose;
-    rf_frame_stats *stats;
-    float *scale;  // r_0 in, r_1 out
-    float4 *pts, *cpts;
-    double *part_S;
-    int *part_n;
-    int max_chunks;
-    int *status;
-    float tau, beta, eps, stop_eps;
-    int k_max, flags;
-};
-
-struct GridSync {
-    unsigned int count;
-    unsigned int gen;
-    int abort;
-    int skip;  // test hook: block 0 leaves at the first barrier without arriving
-};
-
-struct BatchParams {
-    ProblemDesc prob[MAX_BATCH];
-    int B;
-    int k_max_all;
-    int work_warps;
-    GridSync *gs;
-    int *unit_ctr;      // [RF_MAX_ITERS], zero at launch
-    int *block_counts;  // [grid][MAX_BATCH]
-    double *aps;        // [grid][MAX_BATCH][APW]
-    long long timeout_ns;
-};
-
-// ------------------------------------------------------------------ grid barrier
-// Sense-reversing counter barrier over all CTAs of the cooperative launch.  Every
-// wait is bounded: after timeout_ns the CTA sets `abort`, marks every sequence's
-// status RF_ERR_TIMEOUT and returns false; waiters that see `abort` return false.
-__device__ bool grid_barrier(const BatchParams &P)
+static PfoFn pfo_fn(int dtype, int mode, int group)
 {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        GridSync *gs = P.gs;
-        int ok = 1;
-        volatile unsigned int *vgen = &gs->gen;
-        volatile int *vabort = &gs->abort;
-        if (*vabort) {
-            ok = 0;
-        } else if (gs->skip && blockIdx.x == 0) {
-            ok = 0;  // leave without arriving
-        } else {
-            const unsigned int g = *vgen;
-            __threadfence();
-            const unsigned int prev = atomicAdd(&gs->count, 1u);
-            if (prev == gridDim.x - 1) {
-                atomicExch(&gs->count, 0u);
-                __threadfence();
-                atomicAdd(&gs->gen, 1u);
-            } else {
-                const long long t0 = global_ns();
-                unsigned int ns = 32;
-                while (*vgen == g) {
-                    if (*vabort) {
-                        ok = 0;
-                        break;
-                    }
-                    if (global_ns() - t0 > P.timeout_ns) {
-                        atomicExch(&gs->abort, 1);
-                        for (int p = 0; p < P.B; ++p)
-                            atomicCAS(P.prob[p].status, 0, RF_ERR_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(ns);
-                    if (ns < 256)
-                        ns <<= 1;
-                }
-            }
-            __threadfence();
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-// Block-wide exclusive scan of 0/1 flags; returns this thread's prefix and the total.
-__device__ __forceinline__ int block_scan_flag(int flag, int *warp_tot, int *total)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const unsigned b = __ballot_sync(0xffffffffu, flag);
-    const int in_warp = __popc(b & ((1u << lane) - 1u));
-    if (lane == 0)
-        warp_tot[w] = __popc(b);
-    __syncthreads();
-    int before = 0, tot = 0;
-    for (int k = 0; k < nw; ++k) {
-        if (k < w)
-            before += warp_tot[k];
-        tot += warp_tot[k];
-    }
-    __syncthreads();
-    *total = tot;
-    return before + in_warp;
-}
-
-// Merge (max, argmax, second) with another triple; the lowest index wins ties.
-__device__ __forceinline__ void merge_max(float &rm, int &am, float &rs, float om, int oa, float os)
-{
-    float n2 = fmaxf(rs, os);
-    if (om > rm || (om == rm && oa >= 0 && (am < 0 || oa < am))) {
-        n2 = fmaxf(n2, rm);
-        rm = om;
-        am = oa;
-    } else {
-        n2 = fmaxf(n2, om);
-    }
-    rs = n2;
-}
-
-// Per-sequence state, identical in every CTA (computed redundantly in a fixed order).
-struct PState {
-    Pose c, prev;
-    float r[6], r1[6];
-    float rho_carry, rho_ref;
-    int empty_run, stop, active, iters;
-    int level, n_lvl, m_lvl, off_lvl;
-    int nO, offset;
-    int groups, n_chunks, chunk, unit_base;
-    long long lookups;
-};
-
-// ------------------------------------------------------------------ the persistent kernel
-template <int DT, int MODE>
-__global__ void __launch_bounds__(FIT_THREADS, RF_PFO_MIN_BLOCKS) pfo_batch_kernel(const __grid_constant__ BatchParams P)
-{
-    extern __shared__ float4 smem_pts[];
-    __shared__ PState st[MAX_BATCH];
-    __shared__ int warp_tot[FIT_WARPS];
-    __shared__ double red_d[FIT_WARPS][8];
-    __shared__ float red_f[FIT_WARPS][2];
-    __shared__ int red_i[FIT_WARPS][2];
-    __shared__ long long red_v[FIT_WARPS];
-    __shared__ int s_total_units;
-
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int G = gridDim.x, b = blockIdx.x;
-    const int B = P.B;
-
-    // ---- prologue: unproject the points of every level of every sequence (Eq. unproj)
-    {
-        long long total = 0;
-        for (int p = 0; p < B; ++p)
-            total += P.prob[p].m_all;
-        for (long long g = (long long)b * blockDim.x + tid; g < total; g += (long long)G * blockDim.x) {
-            int p = 0;
-            long long base = 0;
-            while (g >= base + P.prob[p].m_all) {
-                base += P.prob[p].m_all;
-                ++p;
-            }
-            const ProblemDesc &pd = P.prob[p];
-            const int j = (int)(g - base);
-            int l = 0;
-            while (l + 1 < pd.n_levels && j >= pd.lvl_off[l + 1])
-                ++l;
-            float4 pt;
-            unproject_point(pd.depth, pd.K, pd.lvl_stride[l], pd.lvl_nw[l], j - pd.lvl_off[l], pt);
-            pd.pts[j] = pt;
-        }
-    }
-    if (tid < B) {
-        const ProblemDesc &pd = P.prob[tid];
-        PState &s = st[tid];
-        const float *c0 = pd.init_pose ? pd.init_pose : pd.prev_pose;
-        for (int a = 0; a < 4; ++a) {
-            s.c.q[a] = __ldcg(&c0[a]);
-            s.prev.q[a] = __ldcg(&pd.prev_pose[a]);
-        }
-        for (int a = 0; a < 3; ++a) {
-            s.c.t[a] = __ldcg(&c0[4 + a]);
-            s.prev.t[a] = __ldcg(&pd.prev_pose[4 + a]);
-        }
-        for (int d = 0; d < 6; ++d)
-            s.r[d] = s.r1[d] = __ldcg(&pd.scale[d]);
-        s.rho_carry = 0.f;
-        s.rho_ref = 0.f;
-        s.empty_run = 0;
-        // stop code 5: skipped by the caller's run flag (never active, writes nothing)
-        s.stop = (pd.run_flag && __ldcg(pd.run_flag) == 0) ? 5 : 0;
-        s.iters = 0;
-        s.lookups = 0;
-    }
-    if (!grid_barrier(P))
-        return;
-
-    for (int k = 1; k <= P.k_max_all; ++k) {
-        if (tid < B) {
-            const ProblemDesc &pd = P.prob[tid];
-            PState &s = st[tid];
-            s.active = (s.stop == 0 && k <= pd.k_max) ? 1 : 0;
-            const int l = (k - 1) % pd.n_levels;
-            s.level = l;
-            s.n_lvl = pd.lvl_n[l];
-            s.m_lvl = pd.lvl_m[l];
-            s.off_lvl = pd.lvl_off[l];
-            if (s.active)
-                s.iters = k;
-        }
-        __syncthreads();
-        int T = 0;
-        bool any = false;
-        for (int p = 0; p < B; ++p)
-            if (st[p].active) {
-                any = true;
-                T += st[p].m_lvl;
-            }
-        if (!any)
-            break;  // identical decision in every CTA
-        // ---- phase A: overlap counts per (CTA, sequence) over the concatenated point sets
-        const int seg = (T + G - 1) / G;
-        const int jb = min(T, b * seg), je = min(T, jb + seg);
-        {
-            int base = 0;
-            for (int p = 0; p < B; ++p) {
-                if (!st[p].active)
-                    continue;
-                const ProblemDesc &pd = P.prob[p];
-                const int lo = max(jb, base), hi = min(je, base + st[p].m_lvl);
-                int cnt = 0;
-                if (lo < hi) {
-                    float Rc[9], Rp[9];
-                    quat_rot(st[p].c.q, Rc);
-                    quat_rot(st[p].prev.q, Rp);
-                    const bool overlap_on = (pd.flags & RF_OVERLAP) != 0;
-                    const float cell_m = (pd.flags & RF_CELL_MARGIN) ? 1.7320508f * pd.V.voxel : 0.f;
-                    for (int j0 = lo; j0 < hi; j0 += blockDim.x) {
-                        const int j = j0 + tid;
-                        int f = 0;
-                        if (j < hi) {
-                            const float4 pt = __ldcg(&pd.pts[st[p].off_lvl + (j - base)]);
-                            f = overlap_on ? overlap_test(pt, Rc, st[p].c.t, Rp, st[p].prev.t, pd.prev_depth, pd.K, cell_m)
-                                           : (pt.w != 0.f);
-                        }
-                        int tot;
-                        block_scan_flag(f, warp_tot, &tot);
-                        cnt += tot;
-                    }
-                }
-                if (tid == 0)
-                    P.block_counts[(size_t)b * MAX_BATCH + p] = cnt;
-                base += st[p].m_lvl;
-            }
-        }
-        if (!grid_barrier(P))
-            return;
-        // ---- phase A': per-sequence offsets and |O_k|, then the compaction
-        for (int p = w; p < B; p += FIT_WARPS) {
-            if (!st[p].active)
-                continue;
-            int before = 0, tot = 0;
-            for (int q = lane; q < G; q += 32) {
-                const int c = __ldcg(&P.block_counts[(size_t)q * MAX_BATCH + p]);
-                tot += c;
-                before += (q < b) ? c : 0;
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                tot += __shfl_xor_sync(0xffffffffu, tot, o);
-                before += __shfl_xor_sync(0xffffffffu, before, o);
-            }
-            if (lane == 0) {
-                st[p].nO = tot;
-                st[p].offset = before;
-            }
-        }
-        __syncthreads();
-        if (tid < B && st[tid].active && st[tid].nO == 0) {  // empty overlap: this sequence stops
-            PState &s = st[tid];
-            s.stop = 4;
-            s.active = 0;
-            if (b == 0) {
-                atomicCAS(P.prob[tid].status, 0, RF_ERR_EMPTY);
-                if (P.prob[tid].stats) {
-                    rf_iter_stats &row = P.prob[tid].stats->it[k - 1];
-                    memset(&row, 0, sizeof row);
-                    row.k = k;
-                    row.stop = 4;
-                    row.level = s.level;
-                    row.n_particles = s.n_lvl;
-                }
-            }
-        }
-        __syncthreads();
-        {
-            int base = 0;
-            for (int p = 0; p < B; ++p) {
-                if (!(st[p].active || (st[p].stop == 4 && st[p].nO == 0 && st[p].iters == k)))
-                    continue;  // only sequences that took part in phase A (their points count in T)
-                const ProblemDesc &pd = P.prob[p];
-                const int lo = max(jb, base), hi = min(je, base + st[p].m_lvl);
-                if (lo < hi && st[p].active) {
-                    float Rc[9], Rp[9];
-                    quat_rot(st[p].c.q, Rc);
-                    quat_rot(st[p].prev.q, Rp);
-                    const bool overlap_on = (pd.flags & RF_OVERLAP) != 0;
-                    const float cell_m = (pd.flags & RF_CELL_MARGIN) ? 1.7320508f * pd.V.voxel : 0.f;
-                    int out = st[p].offset;
-                    for (int j0 = lo; j0 < hi; j0 += blockDim.x) {
-                        const int j = j0 + tid;
-                        int f = 0;
-                        float4 pt = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (j < hi) {
-                            pt = __ldcg(&pd.pts[st[p].off_lvl + (j - base)]);
-                            f = overlap_on ? overlap_test(pt, Rc, st[p].c.t, Rp, st[p].prev.t, pd.prev_depth, pd.K, cell_m)
-                                           : (pt.w != 0.f);
-                        }
-                        int tot;
-                        const int pos = block_scan_flag(f, warp_tot, &tot);
-                        if (f)
-                            pd.cpts[out + pos] = pt;
-                        out += tot;
-                    }
-                }
-                base += st[p].m_lvl;
-            }
-        }
-        if (!grid_barrier(P))
-            return;
-        // ---- phase B: fitness of every particle of every active sequence (Eq. normallh)
-        if (tid == 0) {
-            int units = 0;
-            for (int p = 0; p < B; ++p) {
-                PState &s = st[p];
-                if (!s.active)
-                    continue;
-                const Split sp = make_split(s.n_lvl, s.nO, P.work_warps, P.prob[p].max_chunks);
-                s.groups = sp.groups;
-                s.n_chunks = sp.n_chunks;
-                s.chunk = sp.chunk;
-                s.unit_base = units;
-                units += sp.groups * sp.n_chunks;
-            }
-            s_total_units = units;
-        }
-        __syncthreads();
-        {
-            const int total_units = s_total_units;
-            float4 *spts = smem_pts + (size_t)w * CHUNK_MAX;
-            int *ctr = P.unit_ctr + (k - 1);
-            int t = 0;
-            if (lane == 0)
-                t = atomicAdd(ctr, 1);
-            int u = __shfl_sync(0xffffffffu, t, 0);
-            while (u < total_units) {
-                if (lane == 0)
-                    t = atomicAdd(ctr, 1);
-                const int u_next = __shfl_sync(0xffffffffu, t, 0);
-                // the last active sequence whose first unit is <= u (active bases increase)
-                int p = 0;
-                for (int q = 0; q < B; ++q)
-                    if (st[q].active && st[q].unit_base <= u)
-                        p = q;
-                const PState &s = st[p];
-                const ProblemDesc &pd = P.prob[p];
-                const int local = u - s.unit_base;
-                const int ch = local / s.groups, g = local - ch * s.groups;
-                const int j0 = ch * s.chunk;
-                const int cnt = min(s.chunk, s.nO - j0);
-                __syncwarp();
-                for (int j = lane; j < cnt; j += 32)
-                    spts[j] = __ldcg(&pd.cpts[j0 + j]);
-                __syncwarp();
-                FitParams fp;
-                fp.pst = pd.pst;
-                fp.n = s.n_lvl;
-                fp.ld = pd.n_tmpl;
-                fp.c = s.c;
-                for (int d = 0; d < 6; ++d)
-                    fp.r[d] = s.r[d];
-                fp.l1 = (pd.flags & RF_L1) != 0;
-                fp.right_mult = (pd.flags & RF_RIGHT_MULT) != 0;
-                const int i = g * 32 + lane;
-                double S;
-                int nv;
-                fitness_lane<DT, MODE>(pd.V, spts, cnt, fp, i, S, nv);
-                if (i < s.n_lvl) {
-                    pd.part_S[(size_t)ch * s.n_lvl + i] = S;
-                    pd.part_n[(size_t)ch * s.n_lvl + i] = nv;
-                }
-                u = u_next;
-            }
-        }
-        if (!grid_barrier(P))
-            return;
-        // ---- phase B': per-particle totals, rho, per-CTA APS sums (Eq. ebs, Eq. wafit)
-        for (int p = 0; p < B; ++p) {
-            if (!st[p].active)
-                continue;
-            const ProblemDesc &pd = P.prob[p];
-            const bool normalize = (pd.flags & RF_NORMALIZE) != 0;
-            if (tid == 0) {
-                double S0;
-                int n0;
-                particle_total(pd.part_S, pd.part_n, st[p].n_lvl, st[p].n_chunks, 0, true, S0, n0);
-                const float rho0 = fitness_rho(S0, st[p].nO, pd.tau, normalize);
-                const bool centre = k == 1 || (pd.flags & RF_RHO_REF_CENTER) || pd.n_levels > 1;
-                st[p].rho_ref = centre ? rho0 : st[p].rho_carry;
-            }
-            __syncthreads();
-            const float rho_ref = st[p].rho_ref;
-            // particle 0 is the centre s*_{k-1} itself: an APS candidate only with RF_APS_WITH_CENTRE
-            const int first = (pd.flags & RF_APS_WITH_CENTRE) ? 0 : 1;
-            double sw = 0.0, swr = 0.0, swd[6] = {0, 0, 0, 0, 0, 0};
-            int naps = 0, amax = -1;
-            long long valid = 0;  // valid TSDF samples of all particles (first corner case of Sec. 4)
-            float rmax = -1.f, r2 = -1.f;
-            for (int i = b * blockDim.x + tid; i < st[p].n_lvl; i += G * blockDim.x) {
-                double S;
-                int nv;
-                particle_total(pd.part_S, pd.part_n, st[p].n_lvl, st[p].n_chunks, i, true, S, nv);
-                valid += nv;
-                const float rho = fitness_rho(S, st[p].nO, pd.tau, normalize);
-                merge_max(rmax, amax, r2, rho, i, -1.f);
-                if (i >= first && rho > rho_ref) {
-                    const double wgt = (double)(rho - rho_ref);
-                    ++naps;
-                    sw += wgt;
-                    swr += wgt * (double)rho;
-#pragma unroll
-                    for (int d = 0; d < 6; ++d)
-                        swd[d] += wgt * (double)(st[p].r[d] * __ldg(&pd.pst[(size_t)d * pd.n_tmpl + i]));
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                sw += __shfl_xor_sync(0xffffffffu, sw, o);
-                swr += __shfl_xor_sync(0xffffffffu, swr, o);
-#pragma unroll
-                for (int d = 0; d < 6; ++d)
-                    swd[d] += __shfl_xor_sync(0xffffffffu, swd[d], o);
-                naps += __shfl_xor_sync(0xffffffffu, naps, o);
-                valid += __shfl_xor_sync(0xffffffffu, valid, o);
-                const float om = __shfl_xor_sync(0xffffffffu, rmax, o);
-                const int oa = __shfl_xor_sync(0xffffffffu, amax, o);
-                const float o2 = __shfl_xor_sync(0xffffffffu, r2, o);
-                merge_max(rmax, amax, r2, om, oa, o2);
-            }
-            if (lane == 0) {
-                red_d[w][0] = sw;
-                red_d[w][1] = swr;
-                for (int d = 0; d < 6; ++d)
-                    red_d[w][2 + d] = swd[d];
-                red_i[w][0] = naps;
-                red_i[w][1] = amax;
-                red_f[w][0] = rmax;
-                red_f[w][1] = r2;
-                red_v[w] = valid;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                int na = 0, am = -1;
-                long long nv_all = 0;
-                float rm = -1.f, rs = -1.f;
-                for (int q = 0; q < FIT_WARPS; ++q) {
-                    for (int e = 0; e < 8; ++e)
-                        acc[e] += red_d[q][e];
-                    na += red_i[q][0];
-                    nv_all += red_v[q];
-                    merge_max(rm, am, rs, red_f[q][0], red_i[q][1], red_f[q][1]);
-                }
-                double *out = P.aps + ((size_t)b * MAX_BATCH + p) * APW;
-                for (int e = 0; e < 8; ++e)
-                    out[e] = acc[e];
-                out[8] = (double)na;
-                out[9] = (double)rm;
-                out[10] = (double)am;
-                out[11] = (double)rs;
-                out[12] = (double)nv_all;  // exact: far below 2^53
-            }
-            __syncthreads();
-        }
-        if (!grid_barrier(P))
-            return;
-        // ---- phase C: fixed-order reduction of the APS sums and the PST update
-        for (int p = w; p < B; p += FIT_WARPS) {
-            if (!st[p].active)
-                continue;
-            const ProblemDesc &pd = P.prob[p];
-            PState &s = st[p];
-            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            double na = 0.0, nvalid = 0.0;
-            float rm = -1.f, rs = -1.f;
-            int am = -1;
-            for (int q = lane; q < G; q += 32) {
-                const double *in = P.aps + ((size_t)q * MAX_BATCH + p) * APW;
-                for (int e = 0; e < 8; ++e)
-                    acc[e] += __ldcg(&in[e]);
-                na += __ldcg(&in[8]);
-                nvalid += __ldcg(&in[12]);
-                merge_max(rm, am, rs, (float)__ldcg(&in[9]), (int)__ldcg(&in[10]), (float)__ldcg(&in[11]));
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                for (int e = 0; e < 8; ++e)
-                    acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
-                na += __shfl_xor_sync(0xffffffffu, na, o);
-                nvalid += __shfl_xor_sync(0xffffffffu, nvalid, o);
-                const float om = __shfl_xor_sync(0xffffffffu, rm, o);
-                const int oa = __shfl_xor_sync(0xffffffffu, am, o);
-                const float o2 = __shfl_xor_sync(0xffffffffu, rs, o);
-                merge_max(rm, am, rs, om, oa, o2);
-            }
-            if (lane == 0) {
-                // first corner case of Sec. 4: no particle found a single TSDF sample, so the
-                // likelihood cannot be evaluated: rho = 0.5, v = 1, r_hat = 0.5 v + eps, s* kept
-                const int corner = nvalid == 0.0 ? 1 : (na == 0.0 ? 2 : 0);
-                const int n_aps = corner == 1 ? 0 : (int)na;
-                const float rho_ref = s.rho_ref;
-                float dbar[6], rhat[6];
-                float rho_t;
-                Pose s_new;
-                if (corner == 1) {
-                    rho_t = 0.5f;
-                    for (int d = 0; d < 6; ++d) {
-                        dbar[d] = 0.f;
-                        rhat[d] = (float)(0.5 + (double)pd.eps);
-                    }
-                    s_new = s.c;
-                    s.empty_run += 1;
-                } else if (n_aps > 0) {
-                    double nv2 = 0.0, db[6];
-                    for (int d = 0; d < 6; ++d) {
-                        db[d] = acc[2 + d] / acc[0];
-                        nv2 += db[d] * db[d];
-                    }
-                    const double nv = sqrt(nv2);
-                    rho_t = (float)(acc[1] / acc[0]);
-                    for (int d = 0; d < 6; ++d) {
-                        dbar[d] = (float)db[d];
-                        const double dir = nv < 1e-12 ? 0.40824829046386302 : fabs(db[d]) / nv;
-                        rhat[d] = (float)((1.0 - (double)rho_t) * dir + (double)pd.eps);
-                    }
-                    compose_offset(s.c, dbar, (pd.flags & RF_RIGHT_MULT) != 0, s_new);
-                    s.empty_run = 0;
-                } else {
-                    rho_t = rho_ref;
-                    for (int d = 0; d < 6; ++d) {
-                        dbar[d] = 0.f;
-                        rhat[d] = (float)(2.0 * (1.0 - (double)rho_ref) * 0.40824829046386302 + (double)pd.eps);
-                    }
-                    s_new = s.c;
-                    s.empty_run += 1;
-                }
-                for (int d = 0; d < 6; ++d)
-                    s.r[d] = pd.beta * s.r[d] + (1.f - pd.beta) * rhat[d];
-                s.rho_carry = rho_t;
-                s.c = s_new;
-                if (k == 1)
-                    for (int d = 0; d < 6; ++d)
-                        s.r1[d] = s.r[d];
-                float step = 0.f;
-                for (int d = 0; d < 6; ++d)
-                    step = fmaxf(step, fabsf(dbar[d]));
-                int stop = 0;
-                if (s.empty_run >= 2)
-                    stop = 1;
-                else if (n_aps > 0 && step < pd.stop_eps)
-                    stop = 2;
-                else if (k == pd.k_max)
-                    stop = 3;
-                s.stop = stop;
-                s.lookups += (long long)s.nO * (long long)s.n_lvl;
-                if (b == 0 && pd.stats) {
-                    rf_iter_stats &row = pd.stats->it[k - 1];
-                    row.k = k;
-                    row.n_overlap = s.nO;
-                    row.n_aps = n_aps;
-                    row.argmax = am;
-                    row.rho_ref = rho_ref;
-                    row.rho_tilde = rho_t;
-                    row.rho_max = rm;
-                    row.rho_second = rs;
-                    for (int a = 0; a < 4; ++a)
-                        row.pose[a] = s.c.q[a];
-                    for (int a = 0; a < 3; ++a)
-                        row.pose[4 + a] = s.c.t[a];
-                    for (int d = 0; d < 6; ++d) {
-                        row.scale[d] = s.r[d];
-                        row.offset[d] = dbar[d];
-                    }
-                    row.stop = stop;
-                    row.level = s.level;
-                    row.n_particles = s.n_lvl;
-                    row.corner = corner;
-                }
-            }
-        }
-        __syncthreads();
-    }
-    // ---- epilogue (CTA 0): final poses, r_1 for the next frame, summaries
-    if (b == 0 && tid < B && st[tid].stop != 5) {
-        const ProblemDesc &pd = P.prob[tid];
-        const PState &s = st[tid];
-        for (int a = 0; a < 4; ++a)
-            pd.out_pose[a] = s.c.q[a];
-        for (int a = 0; a < 3; ++a)
-            pd.out_pose[4 + a] = s.c.t[a];
-        for (int d = 0; d < 6; ++d)
-            pd.scale[d] = s.r1[d];
-        if (pd.stats) {
-            pd.stats->iters = s.iters;
-            pd.stats->status = *((volatile int *)pd.status);
-            pd.stats->n_points = pd.lvl_m[0];
-            pd.stats->lookups = s.lookups;
-            for (int d = 0; d < 6; ++d)
-                pd.stats->r1[d] = s.r1[d];
-        }
-    }
+    return dtype == RF_F32 ? pfo_fn_f32(mode, group) : dtype == RF_F16 ? pfo_fn_f16(mode, group) : pfo_fn_i16(mode, group);
 }
 
 __global__ void set_int_kernel(int *dst, int v) { *dst = v; }
@@ -675,32 +39,13 @@ __global__ void set_pose_kernel(float *dst, Pose p)
         dst[4 + a] = p.t[a];
 }
 
-// ------------------------------------------------------------------ kernel table
-using PfoFn = void (*)(BatchParams);
-template <int DT> static PfoFn pfo_fn(int mode)
-{
-    switch (mode) {
-    case 0:
-        return pfo_batch_kernel<DT, 0>;
-    case 1:
-        return pfo_batch_kernel<DT, 1>;
-    case 2:
-        return pfo_batch_kernel<DT, 2>;
-    default:
-        return pfo_batch_kernel<DT, 3>;
-    }
-}
-static PfoFn pfo_fn(int dtype, int mode)
-{
-    return dtype == RF_F32 ? pfo_fn<RF_F32>(mode) : dtype == RF_F16 ? pfo_fn<RF_F16>(mode) : pfo_fn<RF_I16>(mode);
-}
 static int mode_of(int flags) { return ((flags & RF_NEAREST) ? 1 : 0) | ((flags & RF_COMPENSATED) ? 0 : 2); }
 static size_t pfo_smem() { return (size_t)FIT_WARPS * CHUNK_MAX * sizeof(float4); }
 
 // Largest cooperative grid of the kernel variant (CTAs per SM x SMs).
-static rf_status max_ctas_per_sm(int dtype, int mode, int *per_sm)
+static rf_status max_ctas_per_sm(int dtype, int mode, int group, int *per_sm)
 {
-    PfoFn fn = pfo_fn(dtype, mode);
+    PfoFn fn = pfo_fn(dtype, mode, group);
     RF_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pfo_smem()));
     *per_sm = 0;
     RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, (const void *)fn, FIT_THREADS, pfo_smem()));
@@ -778,6 +123,7 @@ struct rf_tracker_s {
     float *depth_ring;  // 2 x max_w * max_h
     int cur;            // ring slot of the previous frame (sequence mode)
     LaunchScratch ls;
+    rf_launch_config cfg;  // launch of this tracker's own frames
     int debug_skip;
     long long timeout_ns;
 };
@@ -870,10 +216,10 @@ static rf_status fill_problem(rf_tracker tr, const float *depth, const float *pr
 // Enqueue one persistent launch for B prepared problems: resets of the barrier,
 // counters, statuses and stats, then the cooperative kernel.  Capturable.
 static rf_status launch_batch(BatchParams &P, const LaunchScratch &ls, int dtype, int mode, int ctas_per_sm,
-                              int debug_skip, cudaStream_t s)
+                              int group, int debug_skip, cudaStream_t s)
 {
     int per_sm = 0;
-    rf_status st = max_ctas_per_sm(dtype, mode, &per_sm);
+    rf_status st = max_ctas_per_sm(dtype, mode, group, &per_sm);
     if (st != RF_OK)
         return st;
     const int use = ctas_per_sm > 0 ? std::min(per_sm, ctas_per_sm) : per_sm;
@@ -896,8 +242,110 @@ static rf_status launch_batch(BatchParams &P, const LaunchScratch &ls, int dtype
         RF_CUDA(cudaGetLastError());
     }
     void *args[] = {&P};
-    RF_CUDA(cudaLaunchCooperativeKernel((const void *)pfo_fn(dtype, mode), dim3(grid), dim3(FIT_THREADS), args,
+    RF_CUDA(cudaLaunchCooperativeKernel((const void *)pfo_fn(dtype, mode, group), dim3(grid), dim3(FIT_THREADS), args,
                                        pfo_smem(), s));
+    return RF_OK;
+}
+
+// Validated copy of a launch configuration (group 0 means the default).
+static rf_status normalise_config(const rf_launch_config *cfg, rf_launch_config *out)
+{
+    RF_CHECK_ARG(cfg->ctas_per_sm >= 0 && cfg->ctas_per_sm <= MAX_CTAS_PER_SM, "ctas_per_sm out of range");
+    RF_CHECK_ARG(cfg->work_warps >= 1 && cfg->work_warps <= WORK_WARPS_MAX, "work_warps out of range");
+    RF_CHECK_ARG(cfg->group == 0 || cfg->group == 4 || cfg->group == 6 || cfg->group == 8,
+                 "group must be 0, 4, 6 or 8");
+    *out = *cfg;
+    if (out->group == 0)
+        out->group = GROUP;
+    return RF_OK;
+}
+
+// Kernel time of one candidate: the faster of two runs (the first warms the caches),
+// the launch's mutable inputs restored before each.
+template <class Run, class Restore>
+static rf_status time_candidate(const rf_launch_config &cand, Run &run, Restore &restore, cudaStream_t s,
+                                cudaEvent_t e0, cudaEvent_t e1, float *ms_out)
+{
+    float best_t = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+        rf_status st = restore();
+        if (st != RF_OK)
+            return st;
+        RF_CUDA(cudaEventRecord(e0, s));
+        st = run(cand);
+        if (st != RF_OK)
+            return st;
+        RF_CUDA(cudaEventRecord(e1, s));
+        RF_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        RF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        best_t = std::min(best_t, ms);
+    }
+    *ms_out = best_t;
+    return RF_OK;
+}
+
+// The candidate search shared by the tracker and batch autotuners: CTAs per SM x
+// work warps {1824, 3648, 7296} with the default group of 6, then groups of 4 and
+// 8 at the best work split (with the best CTAs per SM where that group fits it,
+// and at its own maximum).
+template <class Run, class Restore>
+static rf_status autotune_search(int dtype, int mode, Run &run, Restore &restore, cudaStream_t s,
+                                 rf_launch_config *best_out)
+{
+    cudaEvent_t e0, e1;
+    RF_CUDA(cudaEventCreate(&e0));
+    RF_CUDA(cudaEventCreate(&e1));
+    rf_launch_config best;
+    best.ctas_per_sm = 0;
+    best.work_warps = WORK_WARPS_DEFAULT;
+    best.group = GROUP;
+    best.ms = 1e30f;
+    rf_status st = RF_OK;
+    auto consider = [&](const rf_launch_config &cand) -> rf_status {
+        float ms = 0.f;
+        rf_status r = time_candidate(cand, run, restore, s, e0, e1, &ms);
+        if (r == RF_OK && ms < best.ms) {
+            best = cand;
+            best.ms = ms;
+        }
+        return r;
+    };
+    int per_sm = 0;
+    st = max_ctas_per_sm(dtype, mode, GROUP, &per_sm);
+    const int warps_opts[3] = {WORK_WARPS_DEFAULT / 2, WORK_WARPS_DEFAULT, WORK_WARPS_MAX};
+    for (int c = 1; st == RF_OK && c <= std::min(per_sm, MAX_CTAS_PER_SM); ++c)
+        for (int wi = 0; st == RF_OK && wi < 3; ++wi) {
+            rf_launch_config cand;
+            cand.ctas_per_sm = c;
+            cand.work_warps = warps_opts[wi];
+            cand.group = GROUP;
+            cand.ms = 0.f;
+            st = consider(cand);
+        }
+    if ((mode & 1) == 0) {  // trilinear: the other lookup groups
+        const rf_launch_config base = best;
+        for (int gi = 0; st == RF_OK && gi < 3; ++gi) {
+            const int g = GROUP_CHOICES[gi];
+            if (g == GROUP)
+                continue;
+            int g_per_sm = 0;
+            st = max_ctas_per_sm(dtype, mode, g, &g_per_sm);
+            const int top = std::min(g_per_sm, MAX_CTAS_PER_SM);
+            const int opts[2] = {std::min(base.ctas_per_sm, top), top};
+            for (int k = 0; st == RF_OK && k < (opts[0] == opts[1] ? 1 : 2); ++k) {
+                rf_launch_config cand = base;
+                cand.ctas_per_sm = opts[k];
+                cand.group = g;
+                st = consider(cand);
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != RF_OK)
+        return st;
+    *best_out = best;
     return RF_OK;
 }
 
@@ -939,6 +387,9 @@ rf_status rf_tracker_create(rf_volume v, const float *pst_dev, int n, const rf_p
     tr->max_w = max_width;
     tr->max_h = max_height;
     tr->timeout_ns = 1000000000ll;
+    tr->cfg.ctas_per_sm = 0;
+    tr->cfg.work_warps = WORK_WARPS_DEFAULT;
+    tr->cfg.group = GROUP;
     tr->n_levels = 1;
     tr->lvl_n[0] = n;
     tr->lvl_stride[0] = p->stride;
@@ -1046,9 +497,10 @@ rf_status pfo_track_frame_async(rf_tracker tr, const float *depth_dev, const flo
     if (st != RF_OK)
         return st;
     P.B = 1;
-    P.work_warps = WORK_WARPS_DEFAULT;
+    P.work_warps = tr->cfg.work_warps;
     P.timeout_ns = tr->timeout_ns;
-    st = launch_batch(P, tr->ls, tr->vol->d.dtype, mode_of(tr->p.flags), 0, tr->debug_skip, s);
+    st = launch_batch(P, tr->ls, tr->vol->d.dtype, mode_of(tr->p.flags), tr->cfg.ctas_per_sm, tr->cfg.group,
+                      tr->debug_skip, s);
     if (st != RF_OK)
         return st;
     if (tr->debug_skip) {
@@ -1079,9 +531,9 @@ rf_status pfo_track_frame_ex_async(rf_tracker tr, const float *depth_dev, const 
     if (opt->k_max > 0)
         pd.k_max = opt->k_max;
     P.B = 1;
-    P.work_warps = WORK_WARPS_DEFAULT;
+    P.work_warps = tr->cfg.work_warps;
     P.timeout_ns = tr->timeout_ns;
-    return launch_batch(P, tr->ls, tr->vol->d.dtype, mode_of(tr->p.flags), 0, 0, s);
+    return launch_batch(P, tr->ls, tr->vol->d.dtype, mode_of(tr->p.flags), tr->cfg.ctas_per_sm, tr->cfg.group, 0, s);
 }
 
 rf_status pfo_track_frame(rf_tracker tr, const float *depth_dev, const float *prev_depth_dev, const rf_intrinsics *K,
@@ -1216,7 +668,7 @@ static rf_status batch_enqueue(rf_batch b, int parity, cudaStream_t s)
     rf_status st = batch_params(b, parity, P);
     if (st != RF_OK)
         return st;
-    st = launch_batch(P, b->ls, b->dtype, b->mode, b->cfg.ctas_per_sm, 0, s);
+    st = launch_batch(P, b->ls, b->dtype, b->mode, b->cfg.ctas_per_sm, b->cfg.group, 0, s);
     if (st != RF_OK)
         return st;
     for (int i = 0; i < b->n; ++i) {
@@ -1272,6 +724,7 @@ rf_status rf_batch_create(const rf_tracker *trackers, int n, const rf_intrinsics
     b->mode = mode_of(trackers[0]->p.flags);
     b->cfg.ctas_per_sm = 0;  // as many as fit
     b->cfg.work_warps = WORK_WARPS_DEFAULT;
+    b->cfg.group = GROUP;
     rf_status st = b->ls.alloc();
     cudaError_t e = cudaSuccess;
     if (st == RF_OK) {
@@ -1332,9 +785,11 @@ rf_status rf_batch_start(rf_batch b, const rf_pose *poses_host, void *stream)
 rf_status rf_batch_set_config(rf_batch b, const rf_launch_config *cfg)
 {
     RF_CHECK_ARG(b && cfg, "null pointer");
-    RF_CHECK_ARG(cfg->ctas_per_sm >= 0 && cfg->ctas_per_sm <= MAX_CTAS_PER_SM, "ctas_per_sm out of range");
-    RF_CHECK_ARG(cfg->work_warps >= 1 && cfg->work_warps <= WORK_WARPS_MAX, "work_warps out of range");
-    b->cfg = *cfg;
+    rf_launch_config c;
+    rf_status st = normalise_config(cfg, &c);
+    if (st != RF_OK)
+        return st;
+    b->cfg = c;
     return RF_OK;
 }
 
@@ -1346,7 +801,8 @@ rf_status rf_batch_step(rf_batch b, int parity, int use_graph, void *stream)
     if (!use_graph)
         return batch_enqueue(b, parity, s);
     const bool stale = b->graph[parity] && (b->graph_cfg[parity].ctas_per_sm != b->cfg.ctas_per_sm ||
-                                            b->graph_cfg[parity].work_warps != b->cfg.work_warps);
+                                            b->graph_cfg[parity].work_warps != b->cfg.work_warps ||
+                                            b->graph_cfg[parity].group != b->cfg.group);
     if (stale) {
         cudaGraphExecDestroy(b->graph[parity]);
         b->graph[parity] = nullptr;
@@ -1380,10 +836,6 @@ rf_status rf_batch_autotune(rf_batch b, int parity, rf_launch_config *chosen, vo
     RF_CHECK_ARG(b != nullptr, "null batch");
     RF_CHECK_ARG(parity == 0 || parity == 1, "parity must be 0 or 1");
     cudaStream_t s = (cudaStream_t)stream;
-    int per_sm = 0;
-    rf_status st = max_ctas_per_sm(b->dtype, b->mode, &per_sm);
-    if (st != RF_OK)
-        return st;
     // the PFO launch rewrites each tracker's r_0 and output pose: keep and restore them
     std::vector<float> saved_scale(6 * b->n), saved_pose(7 * b->n);
     for (int i = 0; i < b->n; ++i) {
@@ -1392,58 +844,88 @@ rf_status rf_batch_autotune(rf_batch b, int parity, rf_launch_config *chosen, vo
                                 cudaMemcpyDeviceToHost, s));
     }
     RF_CUDA(cudaStreamSynchronize(s));
-    cudaEvent_t e0, e1;
-    RF_CUDA(cudaEventCreate(&e0));
-    RF_CUDA(cudaEventCreate(&e1));
-    rf_launch_config best = b->cfg;
-    best.ms = 1e30f;
-    const int warps_opts[3] = {WORK_WARPS_DEFAULT / 2, WORK_WARPS_DEFAULT, WORK_WARPS_MAX};
-    for (int c = 1; c <= std::min(per_sm, MAX_CTAS_PER_SM); ++c) {
-        for (int wi = 0; wi < 3; ++wi) {
-            rf_launch_config cand;
-            cand.ctas_per_sm = c;
-            cand.work_warps = warps_opts[wi];
-            float best_t = 1e30f;
-            for (int rep = 0; rep < 2; ++rep) {  // first run warms the caches
-                for (int i = 0; i < b->n; ++i)
-                    RF_CUDA(cudaMemcpyAsync(b->tr[i]->scale, &saved_scale[6 * i], 6 * sizeof(float),
-                                            cudaMemcpyHostToDevice, s));
-                BatchParams P;
-                st = batch_params(b, parity, P);
-                if (st != RF_OK)
-                    break;
-                P.work_warps = cand.work_warps;
-                RF_CUDA(cudaEventRecord(e0, s));
-                st = launch_batch(P, b->ls, b->dtype, b->mode, cand.ctas_per_sm, 0, s);
-                if (st != RF_OK)
-                    break;
-                RF_CUDA(cudaEventRecord(e1, s));
-                RF_CUDA(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                RF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                best_t = std::min(best_t, ms);
-            }
-            if (st != RF_OK)
-                break;
-            if (best_t < best.ms) {
-                best = cand;
-                best.ms = best_t;
-            }
-        }
+    auto restore = [&]() -> rf_status {
+        for (int i = 0; i < b->n; ++i)
+            RF_CUDA(cudaMemcpyAsync(b->tr[i]->scale, &saved_scale[6 * i], 6 * sizeof(float), cudaMemcpyHostToDevice,
+                                    s));
+        return RF_OK;
+    };
+    auto run = [&](const rf_launch_config &cand) -> rf_status {
+        BatchParams P;
+        rf_status st = batch_params(b, parity, P);
         if (st != RF_OK)
-            break;
-    }
+            return st;
+        P.work_warps = cand.work_warps;
+        return launch_batch(P, b->ls, b->dtype, b->mode, cand.ctas_per_sm, cand.group, 0, s);
+    };
+    rf_launch_config best;
+    rf_status st = autotune_search(b->dtype, b->mode, run, restore, s, &best);
     for (int i = 0; i < b->n; ++i) {
         cudaMemcpyAsync(b->tr[i]->scale, &saved_scale[6 * i], 6 * sizeof(float), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(b->tr[i]->pose_ring + 7 * parity, &saved_pose[7 * i], 7 * sizeof(float),
                         cudaMemcpyHostToDevice, s);
     }
     cudaStreamSynchronize(s);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (st != RF_OK)
         return st;
     b->cfg = best;
+    if (chosen)
+        *chosen = best;
+    return RF_OK;
+}
+
+rf_status rf_tracker_set_config(rf_tracker tr, const rf_launch_config *cfg)
+{
+    RF_CHECK_ARG(tr && cfg, "null pointer");
+    rf_launch_config c;
+    rf_status st = normalise_config(cfg, &c);
+    if (st != RF_OK)
+        return st;
+    tr->cfg = c;
+    return RF_OK;
+}
+
+rf_status rf_tracker_get_config(rf_tracker tr, rf_launch_config *cfg)
+{
+    RF_CHECK_ARG(tr && cfg, "null pointer");
+    *cfg = tr->cfg;
+    return RF_OK;
+}
+
+rf_status rf_tracker_autotune(rf_tracker tr, const float *depth_dev, const float *prev_depth_dev,
+                              const rf_intrinsics *K, const float *prev_pose_dev, rf_launch_config *chosen,
+                              void *stream)
+{
+    RF_CHECK_ARG(tr && depth_dev && prev_depth_dev && K && prev_pose_dev, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    float saved_scale[6];
+    RF_CUDA(cudaMemcpyAsync(saved_scale, tr->scale, sizeof saved_scale, cudaMemcpyDeviceToHost, s));
+    RF_CUDA(cudaStreamSynchronize(s));
+    float *out_pose = nullptr;
+    RF_CUDA(cudaMalloc(&out_pose, 7 * sizeof(float)));
+    auto restore = [&]() -> rf_status {
+        RF_CUDA(cudaMemcpyAsync(tr->scale, saved_scale, sizeof saved_scale, cudaMemcpyHostToDevice, s));
+        return RF_OK;
+    };
+    auto run = [&](const rf_launch_config &cand) -> rf_status {
+        BatchParams P;
+        memset(&P, 0, sizeof P);
+        rf_status st = fill_problem(tr, depth_dev, prev_depth_dev, K, prev_pose_dev, out_pose, nullptr, P.prob[0]);
+        if (st != RF_OK)
+            return st;
+        P.B = 1;
+        P.work_warps = cand.work_warps;
+        P.timeout_ns = tr->timeout_ns;
+        return launch_batch(P, tr->ls, tr->vol->d.dtype, mode_of(tr->p.flags), cand.ctas_per_sm, cand.group, 0, s);
+    };
+    rf_launch_config best;
+    rf_status st = autotune_search(tr->vol->d.dtype, mode_of(tr->p.flags), run, restore, s, &best);
+    restore();
+    cudaStreamSynchronize(s);
+    cudaFree(out_pose);
+    if (st != RF_OK)
+        return st;
+    tr->cfg = best;
     if (chosen)
         *chosen = best;
     return RF_OK;

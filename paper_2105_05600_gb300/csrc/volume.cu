@@ -96,16 +96,19 @@ template <typename T> __global__ void brick_to_linear(VolumeDesc V, const T *val
 template <int DT> struct Enc;
 template <> struct Enc<RF_F32> {
     static __device__ __forceinline__ bool unobserved(float v) { return isnan(v); }
+    static __device__ __forceinline__ bool same(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
     static __device__ __forceinline__ float dec(float v) { return v; }
     static __device__ __forceinline__ float enc(float f) { return f; }
 };
 template <> struct Enc<RF_F16> {
     static __device__ __forceinline__ bool unobserved(__half v) { return __hisnan(v); }
+    static __device__ __forceinline__ bool same(__half a, __half b) { return __half_as_ushort(a) == __half_as_ushort(b); }
     static __device__ __forceinline__ float dec(__half v) { return __half2float(v); }
     static __device__ __forceinline__ __half enc(float f) { return __float2half_rn(f); }
 };
 template <> struct Enc<RF_I16> {
     static __device__ __forceinline__ bool unobserved(int16_t v) { return v == I16_UNOBSERVED; }
+    static __device__ __forceinline__ bool same(int16_t a, int16_t b) { return a == b; }
     static __device__ __forceinline__ float dec(int16_t v) { return (float)v * (1.0f / I16_SCALE); }
     static __device__ __forceinline__ int16_t enc(float f)
     {
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(512) integrate_kernel(VolumeDesc V, const floa
         const int b = blockIdx.x * FUSE_BRICKS_PER_CTA + j;
         const int bx = b % V.nb[0], by = (b / V.nb[0]) % V.nb[1], bz = b / (V.nb[0] * V.nb[1]);
         const int x = bx * BRICK + (l & 7), y = by * BRICK + ((l >> 3) & 7), z = bz * BRICK + (l >> 6);
-        bool updated = false;
+        bool updated = false, changed = false;
         do {
             const float pwx = V.origin[0] + V.voxel * ((float)x + 0.5f) - T.t[0];
             const float pwy = V.origin[1] + V.voxel * ((float)y + 0.5f) - T.t[1];
@@ -230,15 +233,19 @@ __global__ void __launch_bounds__(512) integrate_kernel(VolumeDesc V, const floa
             else
                 F_old = Enc<DT>::dec(old);
             const float F_new = ((float)w_old * F_old + f) / (float)(w_old + 1);
-            vals[idx] = Enc<DT>::enc(F_new);
+            const S code = Enc<DT>::enc(F_new);
+            changed = !Enc<DT>::same(code, old);
+            vals[idx] = code;
             V.weights[idx] = (uint8_t)min(w_old + 1, w_max);
             updated = true;
         } while (false);
-        // mark the brick so that its packed cells (and those of the cells reaching
-        // into it from the lower neighbours) are rebuilt
+        // a brick whose stored values changed is marked, so that its packed cells (and
+        // those of the cells reaching into it from the lower neighbours) are rebuilt;
+        // the cells hold values only, so a weight-only update needs no repack
         const int n_updated = __syncthreads_count(updated);
+        const int n_changed = __syncthreads_count(changed);
         if (l == 0) {
-            if (n_updated)
+            if (n_changed)
                 V.dirty[b] = 1;
             atomicAdd(&V.counters[0], (unsigned long long)n_updated);
             atomicAdd(&V.counters[1], 1ull);

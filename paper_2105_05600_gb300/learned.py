@@ -45,18 +45,26 @@ def _tracker(nat, spec, k_max=None, flags=None):
 
 # ----------------------------------------------------------------------------- data
 def generate_dataset(nat, spec: dict, seeds, n_frames: int, substeps: int = 2, group: int = 16,
-                     use_graph: bool = True):
-    """Training pairs from the plain tracker.  Each seeded sequence is rendered at
-    30 Hz x substeps and tracked frame by frame by plain PFO (Algorithm 1, the
-    Sec. 4 initialisation, fusion of every frame; up to `group` sequences per
-    batched step), which keeps its per-frame motion small enough to converge.
-    The samples are the 30 Hz pairs (every substeps-th frame): the network input
-    of (D_t, D_{t-1}, s*_{t-2}, s*_{t-1}) and the target offset(s*_{t-1}, s*_t),
-    s* the tracker's poses (s*_{-1} = s*_0).  Returns dict(X: (N, 832) bfloat16,
-    Y: (N, 6) float32 on the device, seq: (N,) sequence index, tracked / truth:
-    per-sequence 30 Hz poses, seconds)."""
+                     use_graph: bool = True, start: str = "tracked"):
+    """Training pairs from the plain tracker (Algorithm 1 with the Sec. 4
+    initialisation, fusion of every frame; up to `group` sequences per batched
+    step).  The samples are the network input of (D_t, D_{t-1}, s_{t-2},
+    s_{t-1}) and the target offset(s_{t-1}, s*_t), s*_t the pose the tracker
+    converges to for frame t.
+      start="tracked": each seeded sequence is rendered at 30 Hz x substeps and
+        tracked frame by frame, which keeps its per-frame motion small enough to
+        converge; s_{t} are the tracker's own poses at the 30 Hz frames
+        (s_{-1} = s_0).
+      start="truth": rendered at 30 Hz; before each frame the tracker's previous
+        pose is reset to the true pose of frame t-1, so s*_t is what plain PFO
+        converges to from there (and the map is fused at those poses);
+        s_{t-1}, s_{t-2} are the true poses.
+    Returns dict(X: (N, 832) bfloat16, Y: (N, 6) float32 on the device, seq: (N,)
+    sequence index, tracked / truth: per-sequence 30 Hz poses, seconds)."""
     import torch
 
+    if start == "truth":
+        substeps = 1
     seeds = list(seeds)
     n_rows = len(seeds) * (n_frames - 1)
     X = torch.zeros((n_rows, 832), dtype=torch.bfloat16, device="cuda")
@@ -72,6 +80,7 @@ def generate_dataset(nat, spec: dict, seeds, n_frames: int, substeps: int = 2, g
         objs = [_tracker(nat, spec) for _ in gs]
         batch = nat.Batch([o[2] for o in objs], [sq[2] for sq in seqs])
         n = len(gs)
+        gt = torch.as_tensor(np.stack([sq[1] for sq in seqs]), dtype=torch.float32, device="cuda")  # (n, F, 7)
         for i, sq in enumerate(seqs):
             batch.depth_slot(i, 0).copy_(sq[3][0])
         batch.start([sq[1][0] for sq in seqs])
@@ -82,17 +91,20 @@ def generate_dataset(nat, spec: dict, seeds, n_frames: int, substeps: int = 2, g
             par = f % 2
             for i, sq in enumerate(seqs):
                 batch.depth_slot(i, par).copy_(sq[3][f])
+                if start == "truth":
+                    batch.pose_dev(i, 1 - par).copy_(gt[i, f - 1])
             batch.step(par, use_graph=use_graph)
             for i in range(n):
                 poses[i, f].copy_(batch.pose_dev(i, par))
         del batch, objs
+        base = gt if start == "truth" else poses
         for i, sq in enumerate(seqs):
             K, D = sq[2], sq[3]
             for t in range(1, n_frames):
                 a, b = (t - 1) * substeps, t * substeps
                 c = max(a - substeps, 0)
-                nat.rf_proposal_features(D[b], D[a], K, poses[i, c], poses[i, a], x_out=X[row])
-                nat.rf_proposal_target(poses[i, a], poses[i, b], y_out=Y[row])
+                nat.rf_proposal_features(D[b], D[a], K, base[i, c], base[i, a], x_out=X[row])
+                nat.rf_proposal_target(base[i, a], poses[i, b], y_out=Y[row])
                 seq[row] = g0 + i
                 row += 1
         torch.cuda.synchronize()
@@ -126,7 +138,8 @@ def train(nat, X, Y, train_rows, val_rows, epochs: int = 30, batch: int = 512, l
     error of the predicted offset; the network keeps the parameters of the epoch
     with the lowest offset error (the log-scale head overfits long before the
     offset does, so the loss itself would stop too early), then its scale head is
-    calibrated on the held-out rows (calibrate_scale).  Returns (MLP, history)."""
+    calibrated on the held-out rows (rf_mlp_calibrate_scale).  Returns (MLP,
+    history)."""
     import torch
 
     net = nat.MLP(batch)
@@ -151,8 +164,8 @@ def train(nat, X, Y, train_rows, val_rows, epochs: int = 30, batch: int = 512, l
             step += 1
         hist["train"].append(float(losses[step - per_epoch:step].mean().item()))
         hist["val"].append(validation_loss(net, X, Y, va_idx, batch))
-        mu, _, Yv = predict(net, X, Y, va_idx, batch)
-        hist["val_offset_err"].append(float(((mu - Yv) ** 2).sum(1).mean().item()))
+        _, stats = net.evaluate(X, Y, idx=va_idx)
+        hist["val_offset_err"].append(float(stats[0].item()))
         if hist["val_offset_err"][-1] < best:
             best, best_theta = hist["val_offset_err"][-1], net.get_params()
             hist["best_epoch"] = ep
@@ -161,38 +174,20 @@ def train(nat, X, Y, train_rows, val_rows, epochs: int = 30, batch: int = 512, l
     hist["steps"] = step
     if best_theta is not None:
         net.set_params(best_theta)
-    hist["scale_calibration"] = calibrate_scale(net, X, Y, va_idx, batch)
-    hist["zero_offset_err"] = float((Y[va_idx.long()] ** 2).sum(1).mean().item())
+    hist["scale_calibration"] = net.calibrate_scale(X, Y, idx=va_idx)
+    _, stats = net.evaluate(X, Y, idx=va_idx)
+    hist["zero_offset_err"] = float(stats[7:13].sum().item())
     st = net.status()
     if st != 0:
         raise nat.RfError(st, "network kernels reported an error during training")
     return net, hist
 
 
-def predict(net, X, Y, idx, batch: int):
-    """(mean offset mu = previous offset + correction (rows, 6), network outputs
-    (rows, 16), targets (rows, 6)) of the dataset rows idx."""
-    import torch
-
-    outs = torch.cat([net.forward(X[idx[b:b + batch].long()].contiguous()) for b in range(0, len(idx), batch)])
-    v = X[idx.long()][:, N_RES:N_USED_IN].float()
-    return v + outs[:, :6], outs, Y[idx.long()]
-
-
-def calibrate_scale(net, X, Y, va_idx, batch: int):
-    """Per-axis scale calibration on held-out rows: with r = y - mu and the
-    predicted log scale s, k_d^2 = mean(r_d^2 e^{-2 s_d}) is the factor by which
-    the predicted variances are off; adding log k_d to the output bias of s_d
-    makes them match on those rows.  Returns the k_d."""
-    mu, O, Yv = predict(net, X, Y, va_idx, batch)
-    s = O[:, 6:12].clamp(-6.0, 6.0)
-    k2 = (((Yv - mu) ** 2) * (-2.0 * s).exp()).mean(0).double().cpu().numpy()
-    k = np.sqrt(np.maximum(k2, 1e-12))
-    theta = net.get_params()
-    b4 = sum(o * i + o for o, i in LAYERS[:3]) + LAYERS[3][0] * LAYERS[3][1]  # offset of b4
-    theta[b4 + 6:b4 + 12] += np.log(k).astype(np.float32)
-    net.set_params(theta)
-    return [float(v) for v in k]
+def predict(net, X, Y, idx):
+    """(mean offset mu = previous offset + correction (rows, 6), targets (rows, 6))
+    of the dataset rows idx (rf_mlp_evaluate)."""
+    mu, _ = net.evaluate(X, Y, idx=idx)
+    return mu, Y[idx.long()]
 
 
 def validation_loss(net, X, Y, va_idx, batch: int) -> float:
@@ -283,19 +278,24 @@ def run_learned(nat, spec, traj, K, depths, net, params, use_graph=True, warmup=
     timed = st[warmup:]
     return dict(poses=out.cpu().numpy().astype(np.float64), seconds=tm.seconds(n),
                 lookups=sum(s["lookups"] for s in timed), fallbacks=sum(s["used_fallback"] == 1 for s in st),
-                resumed=sum(s["used_fallback"] == 2 for s in st), fallback_kept=sum(s["chose_fallback"] for s in st),
+                resumed=sum(s["used_fallback"] == 2 for s in st), unstuck=sum(s["used_fallback"] == 3 for s in st),
+                fallback_kept=sum(s["chose_fallback"] for s in st),
                 iters=float(np.mean([s["iters_learned"] for s in st])),
                 failed=sum(1 for s in st if s["status"] != 0))
 
 
-def evaluate(nat, spec, seeds, n_frames, net, params, use_graph=True, warmup=0, flush=None):
+def evaluate(nat, spec, seeds, n_frames, net, params, use_graph=True, warmup=0, flush=None, plain=True):
     """A/B on held-out sequences: plain PFO (spec k_max) against the learned
     proposal + k_learned iterations, same frames.  Per sequence: frames/s of the
-    frames after `warmup`, ATE over all tracked frames, lookups, fallbacks."""
+    frames after `warmup`, ATE over all tracked frames, lookups, fallbacks
+    (plain=False skips the plain arm; its entries are then placeholders)."""
     rows = []
     for s in seeds:
         _, traj, K, depths = make_sequence(spec, s, n_frames)
-        pp, tp, lkp = run_plain(nat, spec, traj, K, depths, warmup=warmup, flush=flush)
+        if plain:
+            pp, tp, lkp = run_plain(nat, spec, traj, K, depths, warmup=warmup, flush=flush)
+        else:
+            pp, tp, lkp = np.tile(traj[:1], (len(traj), 1)), 1.0, 0
         rl = run_learned(nat, spec, traj, K, depths, net, params, use_graph, warmup=warmup, flush=flush)
         ap, _ = metrics.ate(pp, traj)
         al, _ = metrics.ate(rl["poses"], traj)
@@ -303,6 +303,6 @@ def evaluate(nat, spec, seeds, n_frames, net, params, use_graph=True, warmup=0, 
         rows.append(dict(seed=s, frames=nf, plain_s=tp, learned_s=rl["seconds"], plain_fps=nf / tp,
                          learned_fps=nf / rl["seconds"], plain_ate_cm=100 * ap, learned_ate_cm=100 * al,
                          plain_lookups=lkp, learned_lookups=rl["lookups"], fallbacks=rl["fallbacks"],
-                         resumed=rl["resumed"],
+                         resumed=rl["resumed"], unstuck=rl["unstuck"],
                          fallback_kept=rl["fallback_kept"], learned_iters=rl["iters"], failed_frames=rl["failed"]))
     return rows

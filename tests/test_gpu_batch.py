@@ -195,7 +195,7 @@ def test_batch_first_frame_matches_oracle(oracle, nat, use_graph):
 
 def test_batch_autotuned_matches_oracle(oracle, nat):
     chosen = _analytic_batch(oracle, nat, SPECS, use_graph=True, autotune=True)
-    assert chosen["ctas_per_sm"] >= 1 and chosen["ms"] > 0
+    assert chosen["ctas_per_sm"] >= 1 and chosen["ms"] > 0 and chosen["group"] in (4, 6, 8)
 
 
 def test_batch_with_an_empty_sequence(nat):

@@ -208,7 +208,7 @@ def test_resume_continues_the_learned_run(nat, tiny):
     tr = nat.Tracker(gv, nat.pst_create(n, seed=1), params, cfg["width"], cfg["height"])
     net = nat.MLP(16)
     net.set_params(zero_network_params(np.log(0.3)))
-    lp = nat.Learned(tr, gv, net, nat.proposal_params(k_learned=1, k_fallback=k_fb, theta=0.0, resume=1),
+    lp = nat.Learned(tr, gv, net, nat.proposal_params(k_learned=1, k_fallback=k_fb, theta=0.0, resume=1, stuck=0),
                      cfg["width"], cfg["height"])
     lp.start(tiny["depths"][0], K, prev)
     sb = nat.new_learned_stats_buffer()
@@ -243,3 +243,42 @@ def test_resume_continues_the_learned_run(nat, tiny):
     want = (pose_f if s["rho_fallback"] > s["rho_learned"] else pose_l).cpu().numpy().astype(np.float64)
     assert s["chose_fallback"] == int(s["rho_fallback"] > s["rho_learned"])
     np.testing.assert_array_equal(np.asarray(pose, dtype=np.float32), want.astype(np.float32))
+
+
+def test_stuck_rule_resumes_from_the_proposal(nat):
+    """A learned run whose every iteration has an empty APS never leaves c_0; with
+    stuck = 1 the second run resumes PFO from c_0 with the carried r_1 of the
+    Sec. 4 initialisation.  On a constant volume every APS is empty, so the
+    learned run stops after two iterations at c_0, the second run starts there
+    with the tracker's r_0 and also stops after two empty iterations.  (Frame 0
+    is an all-invalid depth map, so fusing it leaves the volume constant; the
+    overlap test is off, every valid point is scored.)"""
+    import math
+
+    from test_gpu_tracker import _flat_problem
+
+    flags = nat.RF_NORMALIZE | nat.RF_COMPENSATED
+    r_carry = np.float32([0.011, 0.012, 0.013, 0.021, 0.022, 0.023])
+    net = nat.MLP(16)
+    net.set_params(zero_network_params(np.log(0.3)))
+    sb = nat.new_learned_stats_buffer()
+    runs = {}
+    for stuck in (1, 0):
+        gv, K, depth, pose = _flat_problem(nat, 0.3)
+        tr = nat.Tracker(gv, nat.pst_create(256, seed=1), nat.make_params(k_max=20, flags=flags), 80, 60)
+        tr.set_scale(r_carry)
+        params = nat.proposal_params(k_learned=5, k_fallback=20, theta=0.0, resume=1, stuck=stuck)
+        lp = nat.Learned(tr, gv, net, params, 80, 60)
+        lp.start(np.zeros_like(depth), K, pose)
+        out, status = lp.step(depth, K, stats_dev=sb)
+        runs[stuck] = (nat.learned_stats_dict(sb), out, status, pose)
+    s, out, status, pose = runs[1]
+    assert status == 0 and s["status"] == 0
+    assert s["iters_learned"] == 2 and s["used_fallback"] == 3 and s["iters_fallback"] == 2
+    # zero previous motion: c_0 = s*_{t-1}, and the kept pose is c_0 either way
+    np.testing.assert_array_equal(np.float32(s["init_pose"]), np.float32(pose))
+    np.testing.assert_array_equal(np.float32(out), np.float32(pose))
+    assert abs(s["rho_fallback"] - math.exp(-0.09)) <= 1e-6
+    # with stuck = 0 the learned run is kept and nothing else runs
+    s0 = runs[0][0]
+    assert s0["used_fallback"] == 0 and s0["iters_learned"] == 2 and s0["iters_fallback"] == 0

@@ -40,7 +40,7 @@ def test_trained_proposal_beats_the_zero_offset_and_plain_pfo(nat):
     assert net.status() == 0
     # proposal quality on the held-out sequences' samples
     rows = torch.as_tensor(val_rows.astype(np.int32), device="cuda")
-    mu, _, y = learned.predict(net, ds["X"], ds["Y"], rows, 256)
+    mu, y = learned.predict(net, ds["X"], ds["Y"], rows)
     mu, y = mu.cpu().numpy(), y.cpu().numpy()
     err_net = np.mean(np.sum((mu - y) ** 2, axis=1))
     err_zero = np.mean(np.sum(y ** 2, axis=1))

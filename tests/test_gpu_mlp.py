@@ -325,3 +325,42 @@ def test_target_and_proposal_match_oracle(nat):
             c0[:4] = -c0[:4]
         np.testing.assert_allclose(c0, oc, atol=2e-6)
         np.testing.assert_allclose(r0.cpu().numpy(), orr, rtol=2e-6)
+
+
+# ----------------------------------------------------------------------------- evaluation / calibration
+def test_evaluate_and_calibrate_match_oracle(nat):
+    """rf_mlp_evaluate over gathered rows in several forward batches, and
+    rf_mlp_calibrate_scale, against the oracle.  With dyadic weights, inputs and
+    targets the forward pass and mu are exact (asserted premise), so mu must be
+    equal and the FP64 statistics agree to the rounding of exp."""
+    import torch
+
+    theta, X = dyadic_problem(5, 300)
+    O = assert_exact_premise(theta, X)
+    rng = np.random.default_rng(6)
+    Y = rng.integers(-16, 17, size=(300, 6)) / 16.0
+    idx = rng.permutation(300)[:217].astype(np.int32)
+    net = nat.MLP(64)  # 217 rows in four forward batches
+    net.set_params(theta.astype(np.float32))
+    Xg = to_bf16(X)
+    Yg = torch.from_numpy(Y.astype(np.float32)).cuda()
+    ig = torch.from_numpy(idx).cuda()
+    mu, stats = net.evaluate(Xg, Yg, idx=ig)
+    assert net.status() == 0
+    mu_o, stats_o = mlp.evaluate(theta, X[idx], Y[idx])
+    np.testing.assert_array_equal(mu.cpu().numpy().astype(np.float64), mu_o)
+    np.testing.assert_allclose(stats.cpu().numpy(), stats_o, rtol=1e-12)
+    # calibration: same k, the log-scale biases moved by log k, nothing else changed
+    k = net.calibrate_scale(Xg, Yg, idx=ig)
+    theta_o, k_o = mlp.calibrate_scale(theta.astype(np.float32).astype(np.float64), X[idx], Y[idx])
+    np.testing.assert_allclose(k, k_o, rtol=1e-6)
+    got = net.get_params().astype(np.float64)
+    np.testing.assert_allclose(got, theta_o, rtol=1e-6, atol=1e-7)
+    changed = np.flatnonzero(got != theta.astype(np.float32))
+    assert set(changed) <= set(range(len(theta) - 10, len(theta) - 4))
+    # without an index: the first n rows
+    mu2, stats2 = net.evaluate(Xg, Yg, n_rows=90)
+    theta32 = got
+    mu2_o, stats2_o = mlp.evaluate(theta32, X[:90], Y[:90])
+    np.testing.assert_allclose(mu2.cpu().numpy(), mu2_o, rtol=0, atol=1e-6)
+    np.testing.assert_allclose(stats2.cpu().numpy(), stats2_o, rtol=1e-5)

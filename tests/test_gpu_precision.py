@@ -18,10 +18,21 @@ from paper_2105_05600_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-# relative fitness error bounds derived from the storage step: float32 ~6e-8
-# (FP32 arithmetic dominates: the parity bar), half 2^-11 = 4.9e-4 per value,
-# int16 1/32767 = 3.1e-5 per value (psi^2 errors partly cancel over the points)
-FIT_BOUND = {"f32": 1e-4, "f16": 2e-3, "i16": 5e-4}
+# relative fitness error bounds.  Per stored value the rounding step is 2^-24
+# (float32), 2^-11 relative (half) and 1/32767 absolute (int16); psi^2 doubles a
+# relative error, and over ~4,800 points with rounding errors of both signs the
+# sum's relative error is far below the per-value step (measured on this room:
+# 2.0e-6, 3.8e-5 and 1.0e-5).  The bounds keep 5x margin over those numbers.
+FIT_BOUND = {"f32": 1e-5, "f16": 2e-4, "i16": 5e-5}
+# pose after one tracked frame (up to 12 iterations) against the FP64 oracle on the
+# unrounded TSDF.  Storage rounding moves each fitness by ~1e-5 relative; a
+# candidate that close to the APS threshold joins the APS on one side only, and
+# its weight (below the fitness error) times its offset (a few cm) over the APS
+# weight sum moves s*_k by tens of micrometres, which the later iterations carry.
+# Measured on this frame: 31 um / 5e-4 deg (f32), 101 um / 1.8e-3 deg (f16).
+# A bound of 0.3 mm and 0.01 deg keeps 3x margin and still fails for any error of
+# the path itself (the tracked step is ~10 cm and 5 deg).
+POSE_BOUND_M, POSE_BOUND_DEG = 3e-4, 1e-2
 _REPORT = {}
 
 
@@ -113,4 +124,4 @@ def test_pose_error_vs_fp64(oracle, nat, room, dtype):
     if path:
         with open(path, "w") as f:
             json.dump(_REPORT, f, indent=1)
-    assert dt < 0.02 and dr < 1.0
+    assert dt < POSE_BOUND_M and dr < POSE_BOUND_DEG, (dt, dr)

@@ -106,6 +106,51 @@ def test_tracker_parity_readings(oracle, nat, flags_name):
     print("replay", flags_name, res)
 
 
+@pytest.mark.parametrize("group", [4, 8])
+def test_tracker_parity_lookup_groups(oracle, nat, group):
+    """The kernel variants with 4 and 8 lookups in flight (the default is 6), as
+    the autotuner may pick them, against the oracle iteration by iteration."""
+    import torch
+
+    scene, cfg, gv, ov, traj, K, d0, d1 = _tiny_problem(oracle, nat, "i16")
+    n = cfg["n_particles"]
+    tr = nat.Tracker(gv, nat.pst_create(n, seed=1), nat.make_params(k_max=cfg["k_max"], stride=cfg["stride"]),
+                     cfg["width"], cfg["height"])
+    tr.set_config(ctas_per_sm=0, work_warps=1824, group=group)
+    assert tr.get_config()["group"] == group
+    tr.set_scale([0.1] * 6)
+    prev = pose_f32(traj[0])
+    pose, gst, status = nat.pfo_track_frame(tr, torch.from_numpy(d1).cuda(), torch.from_numpy(d0).cuda(), K, prev)
+    assert status == 0
+    pts = oracle.unproject(d1, K, cfg["stride"])
+    _check_frame(oracle, ov, gst, pose, [(pts, n)], d0, K, prev, prev, np.full(6, np.float32(0.1)), n,
+                 _oracle_params(oracle, cfg["k_max"]), tr)
+
+
+def test_tracker_autotune_then_parity(oracle, nat):
+    """rf_tracker_autotune picks a launch configuration on one frame, restores the
+    tracker's r_0, and the frame tracked with that configuration matches the
+    oracle iteration by iteration."""
+    import torch
+
+    scene, cfg, gv, ov, traj, K, d0, d1 = _tiny_problem(oracle, nat, "i16")
+    n = cfg["n_particles"]
+    tr = nat.Tracker(gv, nat.pst_create(n, seed=1), nat.make_params(k_max=cfg["k_max"], stride=cfg["stride"]),
+                     cfg["width"], cfg["height"])
+    tr.set_scale([0.1] * 6)
+    prev = pose_f32(traj[0])
+    D0, D1 = torch.from_numpy(d0).cuda(), torch.from_numpy(d1).cuda()
+    chosen = tr.autotune(D1, D0, K, torch.from_numpy(prev.astype(np.float32)).cuda())
+    assert chosen["group"] in (4, 6, 8) and chosen["ctas_per_sm"] >= 1 and chosen["ms"] > 0
+    assert tr.get_config() == chosen
+    np.testing.assert_array_equal(tr.get_scale(), np.float32([0.1] * 6))
+    pose, gst, status = nat.pfo_track_frame(tr, D1, D0, K, prev)
+    assert status == 0
+    pts = oracle.unproject(d1, K, cfg["stride"])
+    _check_frame(oracle, ov, gst, pose, [(pts, n)], d0, K, prev, prev, np.full(6, np.float32(0.1)), n,
+                 _oracle_params(oracle, cfg["k_max"]), tr)
+
+
 def _paper_problem(oracle, nat):
     scene, codes, F64, cfg = analytic_volume_codes("paper")
     gv = nat.Volume(cfg["dims"], cfg["voxel"], cfg["trunc"], (0, 0, 0), cfg["dtype"])

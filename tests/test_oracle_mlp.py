@@ -278,3 +278,60 @@ def test_proposal_moves_by_the_predicted_offset():
     c0, r0 = mlp.proposal(o, v, prev)
     np.testing.assert_allclose(c0, cur, atol=1e-12)
     np.testing.assert_allclose(r0, [2e-3, 2e-3, 2e-3, 4e-3, 4e-3, 4e-3])
+
+
+# ----------------------------------------------------------------------------- evaluation / calibration
+def _const_head_network(rng, b_mu, b_s):
+    """A network whose output does not depend on the input: zero weights, output
+    bias (b_mu, b_s) -- mu = previous offset + b_mu, s = b_s on every row."""
+    theta = np.zeros(mlp.n_params())
+    b4 = mlp.unflatten(theta)[7]
+    b4[0:6] = b_mu
+    b4[6:12] = b_s
+    return theta
+
+
+def _rows(rng, B):
+    X = np.zeros((B, mlp.D_IN_PAD))
+    X[:, :mlp.D_IN] = mlp.bf16(rng.normal(size=(B, mlp.D_IN)))
+    Y = rng.normal(size=(B, 6)) * 0.7
+    return X, Y
+
+
+def test_evaluate_agrees_with_the_pinned_loss():
+    # with a constant log scale s, the loss (pinned by finite differences and closed
+    # forms above) is 1/2 stats[0] + 1/2 sum_d stats[1 + d] + sum_d s_d
+    rng = np.random.default_rng(11)
+    X, Y = _rows(rng, 57)
+    b_s = np.array([-0.4, 0.1, 0.3, -1.2, 0.8, 0.05])
+    theta = _const_head_network(rng, rng.normal(size=6) * 0.2, b_s)
+    mu, stats = mlp.evaluate(theta, X, Y)
+    L = mlp.loss(theta, X, Y, round_bf16=True)
+    assert abs(L - (0.5 * stats[0] + 0.5 * stats[1:7].sum() + b_s.sum())) <= 1e-12 * abs(L)
+    # an exact fit: targets equal to mu give zero error
+    mu_fit, stats_fit = mlp.evaluate(theta, X, mu)
+    assert stats_fit[0] == 0.0 and np.all(stats_fit[1:7] == 0.0)
+    np.testing.assert_array_equal(mu_fit, mu)
+    # the zero-offset error of the Sec. 4 initialisation depends on the targets only
+    _, stats_zero = mlp.evaluate(np.zeros(mlp.n_params()), X, Y)
+    np.testing.assert_array_equal(stats_zero[7:13], stats[7:13])
+
+
+def test_calibration_makes_the_moments_one():
+    # k_d^2 = mean e_d^2 exp(-2 s_d); after s_d += log k_d the same mean is exactly 1
+    # (the errors e do not depend on the scale head); a scale head that already fits
+    # gets k = 1
+    rng = np.random.default_rng(12)
+    X, Y = _rows(rng, 200)
+    theta = mlp.init_params(4)
+    b4 = mlp.unflatten(theta)[7]
+    b4[6:12] = rng.normal(size=6) * 0.3
+    theta2, k = mlp.calibrate_scale(theta, X, Y)
+    _, st = mlp.evaluate(theta2, X, Y)
+    np.testing.assert_allclose(st[1:7], 1.0, rtol=1e-12)
+    _, st_before = mlp.evaluate(theta, X, Y)
+    np.testing.assert_allclose(st[0], st_before[0], rtol=1e-15)  # mu unchanged
+    _, k_again = mlp.calibrate_scale(theta2, X, Y)
+    np.testing.assert_allclose(k_again, 1.0, rtol=1e-12)
+    np.testing.assert_array_equal(np.delete(theta2, np.arange(len(theta) - 10, len(theta) - 4)),
+                                  np.delete(theta, np.arange(len(theta) - 10, len(theta) - 4)))

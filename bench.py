@@ -49,11 +49,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-literal", action="store_true", help="skip the paper-literal overlap pass")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
+    ap.add_argument("--storage", choices=["f32", "f16", "i16"], default=None,
+                    help="precision_series config: TSDF storage type (default f16)")
     ap.add_argument("--launch", default=None,
                     help="fixed launch configuration 'ctas_per_sm,work_warps,group' instead of the autotuner")
     ap.add_argument("--train-seqs", type=int, default=None, help="learned config: training sequences")
     ap.add_argument("--train-frames", type=int, default=None, help="learned config: 30 Hz frames per training sequence")
     ap.add_argument("--test-seqs", type=int, default=None, help="learned config: held-out sequences")
+    ap.add_argument("--test-first", type=int, default=0, help="learned config: index of the first held-out seed")
     ap.add_argument("--frames", type=int, default=None,
                     help="frames per sequence (plain configs: the tracked sequence; learned: each held-out one)")
     ap.add_argument("--speed", type=float, default=None, help="learned / ablation config: linear speed (m/s)")
@@ -61,7 +64,7 @@ def parse():
     ap.add_argument("--labels", choices=["tracked", "truth"], default="truth",
                     help="learned config: label frames tracked along the sequence at 60 Hz, or from the true "
                          "previous pose at 30 Hz")
-    ap.add_argument("--proposal", default="kappa=1,theta=0.9,stuck=1",
+    ap.add_argument("--proposal", default="kappa=0.25,theta=0.95,stuck=1",
                     help="learned config: proposal settings 'k=v,...'; several settings separated by ';' are all "
                          "evaluated on the same trained network (the first is the headline)")
     return ap.parse_args()
@@ -755,11 +758,11 @@ def run_learned_bench(args):
         spec["ang_speed"] = args.ang_speed
     n_train = args.train_seqs or len(spec["train_seeds"])
     train_frames = args.train_frames or (1000 if args.labels == "truth" else 500)
-    n_test = args.test_seqs or len(spec["test_seeds"])
+    n_test = args.test_seqs or 4
     frames = args.frames or spec["frames"]
     W = max(3, args.warmup)
     seeds_tr = rank_seeds(spec["train_seeds"][:n_train], rank)
-    seeds_te = rank_seeds(spec["test_seeds"][:n_test], rank)
+    seeds_te = rank_seeds(spec["test_seeds"][args.test_first:args.test_first + n_test], rank)
     ds = learned.generate_dataset(nat, spec, seeds_tr, train_frames, substeps=spec["label_substeps"],
                                   start=args.labels)
     n_val = max(1, n_train // 8)
@@ -968,7 +971,7 @@ def run_mlp_bench(args):
 
 # ----------------------------------------------------------------------------- ablation flags
 ABLATIONS = [("full", 0), ("no_overlap", -1), ("no_normalize", -2), ("no_kahan", -4), ("no_cell_margin", -128),
-             ("nearest", 8), ("rho_ref_centre", 16), ("se3_product", 64)]
+             ("nearest", 8), ("rho_ref_centre", 16), ("se3_product", 64), ("aps_with_centre", 256)]
 
 
 def run_ablation_bench(args):
@@ -1048,6 +1051,8 @@ def run_precision_bench(args):
 
     oracle.build()
     cfg = dict(synth.CONFIGS["precision"])
+    if args.storage:
+        cfg["dtype"] = args.storage
     n_frames = args.frames or cfg["frames"]
     every_fit, every_pose = 50, 200
     seed = cfg["seed"] + rank
@@ -1150,7 +1155,8 @@ def run_precision_bench(args):
     return {
         "metric": METRIC, "value": lookups / t_pfo, "unit": "lookups/s", "n_gpus": 1, "steps": len(timed),
         "warmup": 0, "ms_per_step": 1e3 * t_pfo / max(1, len(timed)), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f16 storage, f32 arithmetic", "data": "synthetic (seeded room and trajectory)",
+        "vs_baseline": None, "dtype": f"{cfg['dtype']} storage, f32 arithmetic",
+        "data": "synthetic (seeded room and trajectory)",
         "config": {"workload": workload_desc(cfg) + f", {n_frames} frames",
                    "oracle": f"FP64 oracle fusing the same frames at the GPU's poses without rounding ({cores} "
                              f"threads); fitness re-scored every {every_fit}th frame (32 particles + s*_t), "

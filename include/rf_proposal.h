@@ -146,10 +146,10 @@ rf_status rf_proposal_target(const float *pose_prev_dev, const float *pose_cur_d
 typedef struct {
     int k_learned;   /* PFO iterations after the proposal (default 5) */
     int k_fallback;  /* iterations of the plain fallback run (default 20) */
-    float kappa;     /* r_0 = kappa * exp(s) * units (default 2) */
+    float kappa;     /* r_0 = kappa * exp(s) * units (default 0.25) */
     float theta;     /* fallback runs when the learned run's final rho_tilde <
                         theta * the previous frame's, or on any error status;
-                        theta < 0: never (default 0.9) */
+                        theta < 0: never (default 0.95) */
     float r_min[6];  /* default 2e-3 (rotation axes), 4e-3 m (translation) */
     float r_max[6];  /* default 0.2, 0.4 m */
     int resume;      /* 1 (default): when the learned run used all k_learned

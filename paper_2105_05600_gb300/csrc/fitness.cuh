@@ -144,6 +144,141 @@ __device__ __forceinline__ void fitness_lane(const VolumeDesc &V, const float4 *
     n_out = nv;
 }
 
+// ------------------------------------------------------------------ packed FP32 pairs
+// Blackwell's FP32 pair instructions (fma/add/sub/mul .f32x2): two independent
+// IEEE operations per instruction, each rounded exactly as its scalar form.  The
+// packed int16 loop below pairs two points of a group and performs, for each of
+// them, the same operations in the same order as the scalar loop, so its results
+// are bit-identical with fewer issued instructions.
+#ifndef RF_PACKED
+#define RF_PACKED 0
+#endif
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_pack(float a, float b)
+{
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t r, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
+{
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_add_rd(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// cell_locate from the biased floor words (bits of __fadd_rd(g, 1.5 * 2^23)).
+__device__ __forceinline__ void cell_locate_int(const CellView &V, int ix, int iy, int iz, unsigned &rec, unsigned &cls)
+{
+    const bool inside = (unsigned)ix < (unsigned)(V.dim[0] - 1) && (unsigned)iy < (unsigned)(V.dim[1] - 1) &&
+                        (unsigned)iz < (unsigned)(V.dim[2] - 1);
+    const unsigned brick =
+        (unsigned)(ix >> 3) + (unsigned)V.nb0 * ((unsigned)(iy >> 3) + (unsigned)V.nb1 * (unsigned)(iz >> 3));
+    rec = brick * (unsigned)BRICK_VOX + (unsigned)((ix & 7) | ((iy & 7) << 3) | ((iz & 7) << 6));
+    cls = inside ? (unsigned)__ldg(&V.cls[brick]) : (unsigned)CELLS_INVALID;
+}
+
+// The int16 trilinear group loop with two points per packed instruction (G even).
+// Per point: the transform, floor and fraction, the class and record loads, the
+// decode and the interpolation of the scalar loop, operation for operation.
+template <int MODE, bool L1, int G>
+__device__ __forceinline__ int fitness_points_i16_packed(const CellView &V, const float4 *spts, int cnt,
+                                                         const float R[9], float t0, float t1, float t2, float &sum,
+                                                         float &comp, int &nv)
+{
+    static_assert(G % 2 == 0, "the packed loop pairs the points of a group");
+    const f2_t R0 = f2_pack(R[0], R[0]), R1 = f2_pack(R[1], R[1]), R2 = f2_pack(R[2], R[2]);
+    const f2_t R3 = f2_pack(R[3], R[3]), R4 = f2_pack(R[4], R[4]), R5 = f2_pack(R[5], R[5]);
+    const f2_t R6 = f2_pack(R[6], R[6]), R7 = f2_pack(R[7], R[7]), R8 = f2_pack(R[8], R[8]);
+    const f2_t T0 = f2_pack(t0, t0), T1 = f2_pack(t1, t1), T2 = f2_pack(t2, t2);
+    const f2_t MAGIC = f2_pack(12582912.0f, 12582912.0f);
+    const f2_t BIAS = f2_pack(8421376.0f, 8421376.0f);  // 2^23 + 32768
+    const f2_t SCALE = f2_pack(1.0f / I16_SCALE, 1.0f / I16_SCALE);
+    int j = 0;
+    for (; j + G <= cnt; j += G) {
+        f2_t FX[G / 2], FY[G / 2], FZ[G / 2];
+        CellRef c[G];
+        CellData<RF_I16> d[G];
+#pragma unroll
+        for (int p = 0; p < G / 2; ++p) {
+            const float4 xa = spts[j + 2 * p], xb = spts[j + 2 * p + 1];
+            const f2_t X = f2_pack(xa.x, xb.x), Y = f2_pack(xa.y, xb.y), Z = f2_pack(xa.z, xb.z);
+            const f2_t GX = f2_fma(R0, X, f2_fma(R1, Y, f2_fma(R2, Z, T0)));
+            const f2_t GY = f2_fma(R3, X, f2_fma(R4, Y, f2_fma(R5, Z, T1)));
+            const f2_t GZ = f2_fma(R6, X, f2_fma(R7, Y, f2_fma(R8, Z, T2)));
+            const f2_t TX = f2_add_rd(GX, MAGIC), TY = f2_add_rd(GY, MAGIC), TZ = f2_add_rd(GZ, MAGIC);
+            FX[p] = f2_sub(GX, f2_sub(TX, MAGIC));
+            FY[p] = f2_sub(GY, f2_sub(TY, MAGIC));
+            FZ[p] = f2_sub(GZ, f2_sub(TZ, MAGIC));
+            float txa, txb, tya, tyb, tza, tzb;
+            f2_unpack(TX, txa, txb);
+            f2_unpack(TY, tya, tyb);
+            f2_unpack(TZ, tza, tzb);
+            cell_locate_int(V, __float_as_int(txa) - 0x4B400000, __float_as_int(tya) - 0x4B400000,
+                            __float_as_int(tza) - 0x4B400000, c[2 * p].rec, c[2 * p].cls);
+            cell_locate_int(V, __float_as_int(txb) - 0x4B400000, __float_as_int(tyb) - 0x4B400000,
+                            __float_as_int(tzb) - 0x4B400000, c[2 * p + 1].rec, c[2 * p + 1].cls);
+        }
+#pragma unroll
+        for (int u = 0; u < G; ++u)
+            cell_fetch<RF_I16>(V, c[u], d[u]);
+        float grp = 0.f;
+#pragma unroll
+        for (int p = 0; p < G / 2; ++p) {
+            const uint4 a = d[2 * p].a, b = d[2 * p + 1].a;
+            // biased corner codes as exact floats 2^23 + u, the two points side by side
+            auto lo = [](uint32_t w) { return __int_as_float((int)__byte_perm(w, 0x4B00u, 0x5410)); };
+            auto hi = [](uint32_t w) { return __int_as_float((int)__byte_perm(w, 0x4B00u, 0x5432)); };
+            const f2_t A0 = f2_pack(lo(a.x), lo(b.x)), A1 = f2_pack(hi(a.x), hi(b.x));
+            const f2_t A2 = f2_pack(lo(a.y), lo(b.y)), A3 = f2_pack(hi(a.y), hi(b.y));
+            const f2_t A4 = f2_pack(lo(a.z), lo(b.z)), A5 = f2_pack(hi(a.z), hi(b.z));
+            const f2_t A6 = f2_pack(lo(a.w), lo(b.w)), A7 = f2_pack(hi(a.w), hi(b.w));
+            const f2_t C00 = f2_fma(FX[p], f2_sub(A1, A0), f2_sub(A0, BIAS));
+            const f2_t C10 = f2_fma(FX[p], f2_sub(A3, A2), f2_sub(A2, BIAS));
+            const f2_t C01 = f2_fma(FX[p], f2_sub(A5, A4), f2_sub(A4, BIAS));
+            const f2_t C11 = f2_fma(FX[p], f2_sub(A7, A6), f2_sub(A6, BIAS));
+            const f2_t Y0 = f2_fma(FY[p], f2_sub(C10, C00), C00);
+            const f2_t Y1 = f2_fma(FY[p], f2_sub(C11, C01), C01);
+            const f2_t VV = f2_mul(f2_fma(FZ[p], f2_sub(Y1, Y0), Y0), SCALE);
+            float va, vb;
+            f2_unpack(VV, va, vb);
+            const bool oka = (a.x & 0xFFFFu) != 0u, okb = (b.x & 0xFFFFu) != 0u;
+            nv += (oka ? 1 : 0) + (okb ? 1 : 0);
+            va = oka ? va : 1.f;
+            vb = okb ? vb : 1.f;
+            grp += L1 ? fabsf(va) : va * va;
+            grp += L1 ? fabsf(vb) : vb * vb;
+        }
+        if (Mode<MODE>::plain)
+            sum += grp;
+        else
+            neumaier_add(sum, comp, grp);
+    }
+    return j;
+}
+
 // The point loop of one lane: lookups of points [0, cnt) under the grid-space
 // pose (R, t), accumulated as psi^2 (|psi| with L1), psi = 1 when invalid.
 template <int DT, int MODE, bool L1, int G>
@@ -162,7 +297,9 @@ __device__ __forceinline__ void fitness_points(const CellView &V, const float4 *
         psi = ok ? psi : 1.f;
         return L1 ? fabsf(psi) : psi * psi;
     };
-    if (!Mode<MODE>::nearest) {
+    if constexpr (RF_PACKED && DT == RF_I16 && !Mode<MODE>::nearest && G % 2 == 0)
+        j = fitness_points_i16_packed<MODE, L1, G>(V, spts, cnt, R, t0, t1, t2, sum, comp, nv);
+    else if (!Mode<MODE>::nearest) {
         // groups of G lookups: all class loads, then all cell loads, then the
         // arithmetic, so each group pays the load latency once; a plain FP32
         // partial of <= G terms in [0, 1] is then added with compensation

@@ -350,8 +350,8 @@ void rf_proposal_default_params(rf_proposal_params *p)
         return;
     p->k_learned = 5;
     p->k_fallback = 20;
-    p->kappa = 2.f;
-    p->theta = 0.9f;
+    p->kappa = 0.25f;
+    p->theta = 0.95f;
     p->resume = 1;
     p->stuck = 1;
     for (int i = 0; i < 6; ++i) {

@@ -55,16 +55,17 @@ def generate_dataset(nat, spec: dict, seeds, n_frames: int, substeps: int = 2, g
         tracked frame by frame, which keeps its per-frame motion small enough to
         converge; s_{t} are the tracker's own poses at the 30 Hz frames
         (s_{-1} = s_0).
-      start="truth": rendered at 30 Hz; before each frame the tracker's previous
-        pose is reset to the true pose of frame t-1, so s*_t is what plain PFO
-        converges to from there (and the map is fused at those poses);
-        s_{t-1}, s_{t-2} are the true poses.
+      start="truth": rendered at 30 Hz; each frame is tracked from the true pose
+        of frame t-1 (one sequence at a time, pfo_track_frame_async) and the
+        map is fused at the true poses, so s*_t is what plain PFO converges to
+        from there on a correct map, and one failed frame does not spoil the
+        frames after it; s_{t-1}, s_{t-2} are the true poses.
     Returns dict(X: (N, 832) bfloat16, Y: (N, 6) float32 on the device, seq: (N,)
     sequence index, tracked / truth: per-sequence 30 Hz poses, seconds)."""
     import torch
 
     if start == "truth":
-        substeps = 1
+        return _dataset_from_truth(nat, spec, seeds, n_frames)
     seeds = list(seeds)
     n_rows = len(seeds) * (n_frames - 1)
     X = torch.zeros((n_rows, 832), dtype=torch.bfloat16, device="cuda")
@@ -80,7 +81,6 @@ def generate_dataset(nat, spec: dict, seeds, n_frames: int, substeps: int = 2, g
         objs = [_tracker(nat, spec) for _ in gs]
         batch = nat.Batch([o[2] for o in objs], [sq[2] for sq in seqs])
         n = len(gs)
-        gt = torch.as_tensor(np.stack([sq[1] for sq in seqs]), dtype=torch.float32, device="cuda")  # (n, F, 7)
         for i, sq in enumerate(seqs):
             batch.depth_slot(i, 0).copy_(sq[3][0])
         batch.start([sq[1][0] for sq in seqs])
@@ -91,13 +91,11 @@ def generate_dataset(nat, spec: dict, seeds, n_frames: int, substeps: int = 2, g
             par = f % 2
             for i, sq in enumerate(seqs):
                 batch.depth_slot(i, par).copy_(sq[3][f])
-                if start == "truth":
-                    batch.pose_dev(i, 1 - par).copy_(gt[i, f - 1])
             batch.step(par, use_graph=use_graph)
             for i in range(n):
                 poses[i, f].copy_(batch.pose_dev(i, par))
         del batch, objs
-        base = gt if start == "truth" else poses
+        base = poses
         for i, sq in enumerate(seqs):
             K, D = sq[2], sq[3]
             for t in range(1, n_frames):
@@ -112,6 +110,42 @@ def generate_dataset(nat, spec: dict, seeds, n_frames: int, substeps: int = 2, g
         tracked += [p for p in sub]
         truth += [sq[1][::substeps] for sq in seqs]
         del seqs
+    return dict(X=X, Y=Y, seq=seq, tracked=tracked, truth=truth, seconds=time.perf_counter() - t0)
+
+
+def _dataset_from_truth(nat, spec, seeds, n_frames):
+    """generate_dataset(start="truth"): per sequence, frame 0 fused at its true
+    pose; every frame t tracked by plain PFO from the true pose of frame t-1
+    (with the tracker's carried r_1) and fused at its true pose."""
+    import torch
+
+    seeds = list(seeds)
+    n_rows = len(seeds) * (n_frames - 1)
+    X = torch.zeros((n_rows, 832), dtype=torch.bfloat16, device="cuda")
+    Y = torch.zeros((n_rows, 6), dtype=torch.float32, device="cuda")
+    seq = np.zeros(n_rows, np.int64)
+    tracked, truth = [], []
+    t0 = time.perf_counter()
+    row = 0
+    for si, s in enumerate(seeds):
+        _, traj, K, D = make_sequence(spec, s, n_frames)
+        vol, pst, tr = _tracker(nat, spec)
+        gt = torch.as_tensor(traj, dtype=torch.float32, device="cuda")
+        poses = torch.zeros_like(gt)
+        poses[0].copy_(gt[0])
+        nat.tsdf_integrate(vol, D[0], K, traj[0])
+        for t in range(1, n_frames):
+            nat.pfo_track_frame_async(tr, D[t], D[t - 1], K, gt[t - 1], poses[t], None)
+            nat.tsdf_integrate_dev(vol, D[t], K, gt[t])
+        for t in range(1, n_frames):
+            nat.rf_proposal_features(D[t], D[t - 1], K, gt[max(t - 2, 0)], gt[t - 1], x_out=X[row])
+            nat.rf_proposal_target(gt[t - 1], poses[t], y_out=Y[row])
+            seq[row] = si
+            row += 1
+        torch.cuda.synchronize()
+        tracked.append(poses.cpu().numpy().astype(np.float64))
+        truth.append(traj)
+        del vol, pst, tr, D
     return dict(X=X, Y=Y, seq=seq, tracked=tracked, truth=truth, seconds=time.perf_counter() - t0)
 
 

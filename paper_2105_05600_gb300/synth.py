@@ -42,7 +42,7 @@ CONFIGS = {
     # then runs k_learned iterations (seeds 100.. train, 1000.. held out)
     "learned": dict(dims=512, voxel=0.01, trunc=0.06, dtype="i16", width=640, height=480, stride=4,
                     n_particles=10000, k_max=20, k_learned=5, frames=1000, speed=4.0, ang_speed=3.0, noise=True,
-                    wall_inset=0.20, seed=0, train_seeds=list(range(100, 132)), test_seeds=list(range(1000, 1004)),
+                    wall_inset=0.20, seed=0, train_seeds=list(range(100, 164)), test_seeds=list(range(1000, 1008)),
                     r_first=[0.05, 0.05, 0.05, 0.15, 0.15, 0.15], label_substeps=2),
 }
 

@@ -104,7 +104,10 @@ def test_proposal_argument_errors_need_no_gpu(built_lib):
     assert n.lib.rf_mlp_forward(None, None, 1, None, None) == n.RF_ERR_ARG
     assert n.lib.rf_mlp_train_step(None, None, None, None, 8, 8, 1e-3, None, None) == n.RF_ERR_ARG
     p = n.proposal_params()
-    assert (p.k_learned, p.k_fallback) == (5, 20) and abs(p.kappa - 2.0) < 1e-7 and abs(p.theta - 0.9) < 1e-7
+    assert (p.k_learned, p.k_fallback, p.resume, p.stuck) == (5, 20, 1, 1)
+    assert abs(p.kappa - 0.25) < 1e-7 and abs(p.theta - 0.95) < 1e-7
+    bad_stuck = n.proposal_params(stuck=3)
+    assert n.lib.rf_learned_create(None, None, None, ctypes.byref(bad_stuck), 8, 8, ctypes.byref(h)) == n.RF_ERR_ARG
     assert n.lib.rf_proposal_apply(None, None, None, ctypes.byref(p), None, None, None) == n.RF_ERR_ARG
     bad = n.proposal_params(k_learned=0)
     assert n.lib.rf_learned_create(None, None, None, ctypes.byref(bad), 8, 8, ctypes.byref(h)) == n.RF_ERR_ARG

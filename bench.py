@@ -532,7 +532,7 @@ def run_ours(args, cfg):
                        "achieved_gbs": fuse_bytes / t_fuse / 1e9, "hbm_frac": fuse_bytes / t_fuse / 1e9 / hbm,
                        "note": f"{2 * (vbytes + 1)} B per updated voxel (value + weight, read and written) + "
                                f"{512 * 9 * vbytes} B per repacked brick (cell records written, values read)"},
-            "gpu_launches": 3 * K_steps,  # per step: pfo_batch_kernel, integrate_kernel, pack_cells_kernel
+            "gpu_launches": 4 * K_steps,  # per step: pfo_batch_kernel, cull_bricks, integrate, pack_cells
             "clocks": clk,
         }
         if lit is not None:
@@ -717,7 +717,7 @@ def run_batched(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "whole step (batched pfo kernel + 16 x fusion)",
                          "note": f"16 B per lookup over the whole graph time, {peak_kind} HBM copy peak"},
-            "gpu_launches": K_steps * (1 + 2 * len(seqs)),
+            "gpu_launches": K_steps * (1 + 3 * len(seqs)),
             "clocks": clk,
         }
         if e2e is not None:
@@ -889,7 +889,7 @@ def run_learned_bench(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "whole learned step (proposal + pfo_batch_kernel x2 + fusion)",
                      "note": f"16 B per lookup over the whole step time, {peak_kind} HBM copy peak"},
-        "gpu_launches": 12 * nf,  # features, 4 GEMMs, apply, 2 PFO, judge, select, integrate, pack
+        "gpu_launches": 13 * nf,  # features, 4 GEMMs, apply, 2 PFO, judge, select, cull, integrate, pack
         "clocks": clk,
     }
     if e2e is not None:
@@ -1019,7 +1019,7 @@ def run_ablation_bench(args):
         "config": {"workload": f"ablation of plain PFO: 512^3 int16, 640x480 stride 4, 10000 particles, <= 20 "
                                f"iterations, {spec['speed']:g} m/s + {spec['ang_speed']:g} rad/s, {len(seqs)} sequences "
                                f"x {frames} frames", "l2": "flushed before every timed frame"},
-        "ablation": table, "gpu_launches": 3 * len(ABLATIONS) * len(seqs) * (frames - 1 - W), "clocks": clk,
+        "ablation": table, "gpu_launches": 4 * len(ABLATIONS) * len(seqs) * (frames - 1 - W), "clocks": clk,
     }
 
 
@@ -1166,7 +1166,7 @@ def run_precision_bench(args):
                               "selected_pose": summary("S_rel_selected")},
         "pose_vs_fp64": {"translation_m": summary("pose_dt_m"), "rotation_deg": summary("pose_dr_deg")},
         "series": series, "ate_cm": {"mean": 100 * ate[0], "rmse": 100 * ate[1], "frames": n_frames - 1},
-        "wall_s": wall, "gpu_launches": 3 * (n_frames - 1),
+        "wall_s": wall, "gpu_launches": 4 * (n_frames - 1),
     }
 
 

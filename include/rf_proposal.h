@@ -148,8 +148,10 @@ typedef struct {
     int k_fallback;  /* iterations of the plain fallback run (default 20) */
     float kappa;     /* r_0 = kappa * exp(s) * units (default 0.25) */
     float theta;     /* fallback runs when the learned run's final rho_tilde <
-                        theta * the previous frame's, or on any error status;
-                        theta < 0: never (default 0.95) */
+                        theta * the previous frame's, on any error status, or
+                        when its first iteration found no TSDF sample for any
+                        particle (Sec. 4's first corner case: the proposal is off
+                        the map); theta < 0: never (default 0.95) */
     float r_min[6];  /* default 2e-3 (rotation axes), 4e-3 m (translation) */
     float r_max[6];  /* default 0.2, 0.4 m */
     int resume;      /* 1 (default): when the learned run used all k_learned
@@ -188,7 +190,8 @@ rf_status rf_proposal_apply(const float *out_dev, const uint16_t *x_dev, const f
  *   k_fallback iterations; else if the run never left c_0, the `stuck` rule;
  *   else, with `resume`, if the learned run stopped at k_learned unconverged,
  *   PFO continues from its s* and axis lengths for up to k_fallback
- *   iterations; the result with the higher final rho_tilde is kept -> fusion
+ *   iterations; the result with the higher final rho_tilde is kept (a tie goes
+ *   to a plain restart, else to the learned run) -> fusion
  *   (tsdf_integrate) of D_t at the kept pose.
  * Frames are at most max_width x max_height.  The tracker and network must not
  * be used by other calls while a step runs.

@@ -166,7 +166,10 @@ rf_status rf_volume_info(rf_volume v, int dims[3], float *voxel, float *trunc, f
  * is averaged in: F <- (W F + f) / (W + 1), W <- min(W + 1, 255).
  *   depth_dev   device float[K->height * K->width], metres, row-major.
  *   K, pose     host structs.
- * Asynchronous.
+ * Asynchronous: four stream-ordered operations (list reset, frustum culling,
+ * update of the visible bricks, repacking of the cells that read a changed
+ * value).  The volume holds one set of work lists, so fusions into the same
+ * volume must not run concurrently on different streams.
  */
 rf_status tsdf_integrate(rf_volume v, const float *depth_dev, const rf_intrinsics *K, const rf_pose *pose,
                          void *stream);

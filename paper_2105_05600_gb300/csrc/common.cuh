@@ -43,10 +43,18 @@ struct VolumeDesc {
     // Packed trilinear cells: record i (same brick index as voxel i) holds the 8
     // corner codes of the cell whose lower corner is voxel i, ordered
     // (x,y,z) = 000,100,010,110,001,101,011,111: 16 B for int16/half, 32 B for
-    // float.  Rebuilt from `values` for every brick marked in `dirty`.
+    // float.  Fusion rebuilds the cells of every brick that reads a changed value.
     // int16 cells hold the biased code c + 32768 (sentinel -> 0).
     void *cells;
-    uint8_t *dirty;    // one flag per brick, set by fusion, cleared after packing
+    // Fusion work lists, rebuilt by every tsdf_integrate: fuse_count[0] bricks that
+    // passed the frustum test, listed in fuse_list[0, nbricks); fuse_count[1] bricks
+    // whose cells are to be repacked, listed in fuse_list[nbricks, 2 nbricks) and
+    // marked in the bit set `need` (one bit per brick, so a brick is listed once).
+    // fuse_count and need are one allocation, cleared together before each fusion.
+    unsigned *fuse_count;
+    uint32_t *need;
+    int *fuse_list;
+    int fuse_grid[2];  // persistent grid (CTAs) of integrate_kernel and pack_cells_kernel
     // Class of each cell brick, written with its cells: CELLS_MIXED, or every
     // cell of the brick free space (all 8 corners exactly +1: psi = 1, valid) or
     // every cell touching an unobserved voxel (invalid).  Lookups in constant
@@ -301,13 +309,33 @@ __device__ __forceinline__ void cell_locate(const CellView &V, float gx, float g
 #endif
 }
 
-// The record of a constant brick is not loaded: the registers get a fill
-// record that evaluates to the same answer (eight +1 corners for free space,
-// an invalid record otherwise), and the load is predicated on a mixed brick.
+// The record of a constant brick is not loaded (the load is predicated on a
+// mixed brick); the registers get a fill that evaluates to the brick's answer.
+// float / half: eight +1 corners for free space, NaN corners otherwise.
+// int16 (RF_I16_MARKER = 1, the default): only the first word is filled, with
+// 0xFFFF0000 for free space and 0 otherwise; the other three keep whatever they
+// held.  A packed int16 record whose first corner is the unobserved code is all
+// zero, so a first word with a zero low half and a non-zero high half never
+// occurs in the cells and marks free space (psi = 1, valid) for cell_eval.
+// RF_I16_MARKER = 0 fills all four words (eight +1 corners or zeros), as for
+// the other types.  Both give the same results: an all-+1 int16 cell
+// interpolates to psi = 1 exactly.
+#ifndef RF_I16_MARKER
+#define RF_I16_MARKER 1
+#endif
+constexpr uint32_t I16_FREE_MARKER = 0xFFFF0000u;
 __device__ __forceinline__ void ldg_v4_if(bool p, const void *ptr, uint32_t &x, uint32_t &y, uint32_t &z, uint32_t &w)
 {
     asm("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t@p ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%5];\n\t}"
         : "+r"(x), "+r"(y), "+r"(z), "+r"(w)
+        : "r"((int)p), "l"(ptr));
+}
+// the same load with only the first word filled beforehand
+__device__ __forceinline__ void ldg_v4_if_x(bool p, const void *ptr, uint32_t &x, uint32_t &y, uint32_t &z,
+                                            uint32_t &w)
+{
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t@p ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%5];\n\t}"
+        : "+r"(x), "=r"(y), "=r"(z), "=r"(w)
         : "r"((int)p), "l"(ptr));
 }
 
@@ -338,6 +366,10 @@ template <int DT> __device__ __forceinline__ void cell_fetch(const CellView &V, 
         ldg_v4_if(mixed, cp + 1, b0, b1, b2, b3);
         d.a = make_float4(__uint_as_float(a0), __uint_as_float(a1), __uint_as_float(a2), __uint_as_float(a3));
         d.b = make_float4(__uint_as_float(b0), __uint_as_float(b1), __uint_as_float(b2), __uint_as_float(b3));
+    } else if (DT == RF_I16 && RF_I16_MARKER) {
+        uint32_t x = free_space ? I16_FREE_MARKER : 0u, y, z, w;
+        ldg_v4_if_x(mixed, reinterpret_cast<const uint4 *>(V.cells) + c.rec, x, y, z, w);
+        d.a = make_uint4(x, y, z, w);
     } else {
         // int16 (biased): 0xFFFF = code +32767, 0 = invalid; half: 1.0h pairs, NaN pairs
         const uint32_t f = DT == RF_I16 ? (free_space ? 0xFFFFFFFFu : 0u) : (free_space ? 0x3C003C00u : 0x7E007E00u);
@@ -347,6 +379,8 @@ template <int DT> __device__ __forceinline__ void cell_fetch(const CellView &V, 
     }
 }
 
+// Returns whether the lookup is valid; psi is the interpolated value when valid
+// and 1 (the maximal truncated penalty) when not.
 template <int DT> __device__ __forceinline__ bool cell_eval(const CellRef &c, const CellData<DT> &d, float &psi)
 {
     float c00, c10, c01, c11;
@@ -392,7 +426,9 @@ template <int DT> __device__ __forceinline__ bool cell_eval(const CellRef &c, co
         v *= 1.0f / I16_SCALE;
     else
         ok = !isnan(v);  // a NaN corner poisons the interpolation
-    psi = v;
+    psi = ok ? v : 1.f;
+    if constexpr (DT == RF_I16 && RF_I16_MARKER)
+        return ok || d.a.x == I16_FREE_MARKER;  // free space: psi = 1, valid
     return ok;
 }
 

@@ -264,10 +264,14 @@ __device__ __forceinline__ int fitness_points_i16_packed(const CellView &V, cons
             const f2_t VV = f2_mul(f2_fma(FZ[p], f2_sub(Y1, Y0), Y0), SCALE);
             float va, vb;
             f2_unpack(VV, va, vb);
-            const bool oka = (a.x & 0xFFFFu) != 0u, okb = (b.x & 0xFFFFu) != 0u;
-            nv += (oka ? 1 : 0) + (okb ? 1 : 0);
+            bool oka = (a.x & 0xFFFFu) != 0u, okb = (b.x & 0xFFFFu) != 0u;
             va = oka ? va : 1.f;
             vb = okb ? vb : 1.f;
+            if (RF_I16_MARKER) {  // free space (as cell_eval)
+                oka = oka || a.x == I16_FREE_MARKER;
+                okb = okb || b.x == I16_FREE_MARKER;
+            }
+            nv += (oka ? 1 : 0) + (okb ? 1 : 0);
             grp += L1 ? fabsf(va) : va * va;
             grp += L1 ? fabsf(vb) : vb * vb;
         }
@@ -292,9 +296,8 @@ __device__ __forceinline__ void fitness_points(const CellView &V, const float4 *
         else
             neumaier_add(sum, comp, grp);
     };
-    auto term = [&](bool ok, float psi) {
+    auto term = [&](bool ok, float psi) {  // psi = 1 when invalid (cell_eval, nearest below)
         nv += ok ? 1 : 0;
-        psi = ok ? psi : 1.f;
         return L1 ? fabsf(psi) : psi * psi;
     };
     if constexpr (RF_PACKED && DT == RF_I16 && !Mode<MODE>::nearest && G % 2 == 0)
@@ -335,6 +338,7 @@ __device__ __forceinline__ void fitness_points(const CellView &V, const float4 *
         bool ok;
         if (Mode<MODE>::nearest) {
             ok = sample_nearest_g<DT>(V, gx, gy, gz, psi);
+            psi = ok ? psi : 1.f;
         } else {
             CellRef c;
             CellData<DT> d;

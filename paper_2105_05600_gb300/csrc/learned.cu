@@ -176,16 +176,21 @@ struct LearnedState {
 };
 
 // Second run of a frame: a plain restart from s*_{t-1} with the carried r_1 when
-// the learned run failed or its final rho_tilde fell below theta x the previous
-// frame's; otherwise, with `resume`, a continuation from the learned run's state
-// (its s* and axis lengths) when that run used all k_learned iterations without
-// meeting a convergence criterion of Sec. 4 (stop reason k_max).
+// the learned run failed, its final rho_tilde fell below theta x the previous
+// frame's, or its first iteration found no TSDF sample for any particle (the
+// first corner case of Sec. 4: the proposal lies off the map, where every
+// particle scores alike and PFO cannot leave c_0, so keeping it would let the
+// next proposal extrapolate the jump); otherwise, with `resume`, a continuation
+// from the learned run's state (its s* and axis lengths) when that run used all
+// k_learned iterations without meeting a convergence criterion of Sec. 4 (stop
+// reason k_max).
 __global__ void judge_kernel(LearnedState *S, float theta, int resume, int stuck)
 {
     const rf_frame_stats &l = S->st_l;
     const float rho = final_rho(&l);
     const int last = min(l.iters, RF_MAX_ITERS) - 1;
-    const bool bad = l.status != 0 || l.iters == 0 || rho < theta * S->rho_prev;
+    const bool off_map = l.iters > 0 && l.it[0].corner == 1;
+    const bool bad = l.status != 0 || l.iters == 0 || rho < theta * S->rho_prev || off_map;
     const bool open = last >= 0 && l.it[last].stop == 3;
     bool moved = false;  // some iteration had a non-empty APS, i.e. s* left c_0
     for (int k = 0; k <= last; ++k)
@@ -212,7 +217,9 @@ __global__ void select_kernel(LearnedState *S, rf_learned_stats *out_stats, floa
     const rf_frame_stats &l = S->st_l, &f = S->st_f;
     const float rl = final_rho(&l), rfb = final_rho(&f);
     const bool ran = S->run_flag != 0 && f.iters > 0;
-    const bool take_f = ran && f.status == 0 && (l.status != 0 || rfb > rl);
+    // the higher final rho_tilde wins; a tie goes to a plain restart (the method's
+    // own tracker from s*_{t-1}), otherwise to the learned run
+    const bool take_f = ran && f.status == 0 && (l.status != 0 || rfb > rl || (S->run_flag == 1 && rfb == rl));
     const float *p = take_f ? S->pose_f : S->pose_l;
     if (out_stats) {
         out_stats->status = take_f ? f.status : l.status;

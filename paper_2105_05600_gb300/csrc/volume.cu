@@ -8,6 +8,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 
 #include "common.cuh"
@@ -118,10 +119,6 @@ template <> struct Enc<RF_I16> {
     }
 };
 
-// Bricks handled by one CTA of the fusion kernels (one brick per loop step).
-constexpr int FUSE_BRICKS_PER_CTA = 8;
-static_assert(FUSE_BRICKS_PER_CTA == 8, "the dirty-flag scan of pack_cells_kernel maps 8 bricks x 8 neighbours to warp 0");
-
 // Conservative test of whether brick (bx, by, bz) can hold a voxel that the
 // per-voxel fusion test accepts: the sphere around the brick's voxel centres
 // (radius 3.5 sqrt(3) voxels, plus a margin far above FP32 rounding) must meet
@@ -156,49 +153,66 @@ __device__ __forceinline__ bool brick_may_update(const VolumeDesc &V, int bx, in
     return true;
 }
 
-// Projective TSDF fusion (Sec. 3 overview; Curless & Levoy 1996, KinectFusion
-// 2011).  Each CTA walks FUSE_BRICKS_PER_CTA consecutive 8x8x8 bricks with one
-// thread per voxel, so value and weight accesses are contiguous 1 KiB (or 2 KiB)
-// runs; thread 0 first tests the brick against the view frustum and the depth
-// range (brick_may_update) and the CTA skips bricks that cannot change.  Per
-// updated voxel 2+2 B of value (4+4 for float) and 1+1 B of weight plus the
-// depth reads.  The pose comes by value, or from device memory (pose_dev !=
-// NULL, written by the tracker earlier on the stream); a non-zero *status_dev
-// skips the update.
-template <int DT>
-__global__ void __launch_bounds__(512) integrate_kernel(VolumeDesc V, const float *__restrict__ depth, Intr K, Pose T,
-                                                        const float *pose_dev, const int *status_dev, int w_max,
-                                                        int nbricks)
+__device__ __forceinline__ void load_pose(Pose &T, const float *pose_dev)
 {
-    using S = typename Storage<DT>::T;
-    if (status_dev && *((volatile const int *)status_dev) != 0)
-        return;
     if (pose_dev) {
         for (int a = 0; a < 4; ++a)
             T.q[a] = pose_dev[a];
         for (int a = 0; a < 3; ++a)
             T.t[a] = pose_dev[4 + a];
     }
+}
+
+// Frustum culling, one thread per brick: the bricks that brick_may_update
+// accepts are appended to the visible list (one atomic per warp).  The order of
+// the list is immaterial: each listed brick is updated by one CTA, alone.  The
+// pose comes by value, or from device memory (pose_dev != NULL, written by the
+// tracker earlier on the stream); a non-zero *status_dev lists nothing, so the
+// fusion that follows changes nothing.
+__global__ void __launch_bounds__(256) cull_bricks_kernel(VolumeDesc V, Intr K, Pose T, const float *pose_dev,
+                                                          const int *status_dev, int nbricks)
+{
+    if (status_dev && *((volatile const int *)status_dev) != 0)
+        return;
+    load_pose(T, pose_dev);
     float R[9];
     quat_rot(T.q, R);
-    // lane j of warp 0 tests brick j of this CTA; one barrier publishes the mask
-    __shared__ unsigned s_visible;
-    const int l = threadIdx.x;
-    if (l < 32) {
-        const int b = blockIdx.x * FUSE_BRICKS_PER_CTA + l;
-        bool vis = false;
-        if (l < FUSE_BRICKS_PER_CTA && b < nbricks)
-            vis = brick_may_update(V, b % V.nb[0], (b / V.nb[0]) % V.nb[1], b / (V.nb[0] * V.nb[1]), R, T.t, K);
-        const unsigned m = __ballot_sync(0xffffffffu, vis);
-        if (l == 0)
-            s_visible = m;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vis = b < nbricks &&
+                     brick_may_update(V, b % V.nb[0], (b / V.nb[0]) % V.nb[1], b / (V.nb[0] * V.nb[1]), R, T.t, K);
+    const unsigned m = __ballot_sync(0xffffffffu, vis);
+    if (m == 0u)
+        return;  // warp-uniform
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0u;
+    if (lane == 0) {
+        base = atomicAdd(&V.fuse_count[0], (unsigned)__popc(m));
+        atomicAdd(&V.counters[1], (unsigned long long)__popc(m));
     }
-    __syncthreads();
-    const unsigned visible = s_visible;
-    for (int j = 0; j < FUSE_BRICKS_PER_CTA; ++j) {
-        if (!((visible >> j) & 1u))
-            continue;  // uniform across the CTA (also every brick past the end)
-        const int b = blockIdx.x * FUSE_BRICKS_PER_CTA + j;
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (vis)
+        V.fuse_list[base + __popc(m & ((1u << lane) - 1u))] = b;
+}
+
+// Projective TSDF fusion (Sec. 3 overview; Curless & Levoy 1996, KinectFusion
+// 2011) of the bricks on the visible list.  A persistent grid walks the list,
+// one 8x8x8 brick per CTA step with one thread per voxel, so value and weight
+// accesses are contiguous 1 KiB (or 2 KiB) runs.  Per updated voxel 2+2 B of
+// value (4+4 for float) and 1+1 B of weight plus the depth read.  A brick whose
+// stored value codes changed puts the bricks whose cells read it (itself and
+// its lower neighbours, b - {0,1}^3) on the repack list, each once.
+template <int DT>
+__global__ void __launch_bounds__(512, 4) integrate_kernel(VolumeDesc V, const float *__restrict__ depth, Intr K, Pose T,
+                                                        const float *pose_dev, int w_max, int nbricks)
+{
+    using S = typename Storage<DT>::T;
+    load_pose(T, pose_dev);
+    float R[9];
+    quat_rot(T.q, R);
+    const int l = threadIdx.x;
+    const int n_visible = (int)V.fuse_count[0];
+    for (int i = blockIdx.x; i < n_visible; i += gridDim.x) {
+        const int b = V.fuse_list[i];
         const int bx = b % V.nb[0], by = (b / V.nb[0]) % V.nb[1], bz = b / (V.nb[0] * V.nb[1]);
         const int x = bx * BRICK + (l & 7), y = by * BRICK + ((l >> 3) & 7), z = bz * BRICK + (l >> 6);
         bool updated = false, changed = false;
@@ -239,35 +253,66 @@ __global__ void __launch_bounds__(512) integrate_kernel(VolumeDesc V, const floa
             V.weights[idx] = (uint8_t)min(w_old + 1, w_max);
             updated = true;
         } while (false);
-        // a brick whose stored values changed is marked, so that its packed cells (and
-        // those of the cells reaching into it from the lower neighbours) are rebuilt;
         // the cells hold values only, so a weight-only update needs no repack
         const int n_updated = __syncthreads_count(updated);
         const int n_changed = __syncthreads_count(changed);
-        if (l == 0) {
-            if (n_changed)
-                V.dirty[b] = 1;
-            atomicAdd(&V.counters[0], (unsigned long long)n_updated);
-            atomicAdd(&V.counters[1], 1ull);
+        if (n_changed && l < 8) {
+            const int nx = bx - (l & 1), ny = by - ((l >> 1) & 1), nz = bz - (l >> 2);
+            if (nx >= 0 && ny >= 0 && nz >= 0) {
+                const int nbk = nx + V.nb[0] * (ny + V.nb[1] * nz);
+                const uint32_t bit = 1u << (nbk & 31);
+                if (!(atomicOr(&V.need[nbk >> 5], bit) & bit))
+                    V.fuse_list[nbricks + (int)atomicAdd(&V.fuse_count[1], 1u)] = nbk;
+            }
         }
+        if (l == 0)
+            atomicAdd(&V.counters[0], (unsigned long long)n_updated);
     }
 }
 
 // Packed trilinear cells of one brick (one thread per cell) and its class.
 // Cell i reads voxels i + {0,1}^3; cells on the upper faces of the volume are
-// never sampled and copy the nearest voxels.
+// never sampled and copy the nearest voxels.  The CTA first stages the 9x9x9
+// voxels its cells read in shared memory: the brick itself (one contiguous
+// load per thread) and the 217 voxels of its upper x, y and z faces, edges and
+// corner (threads 0..216), each clamped to the volume like the corners.
+constexpr int HALO = BRICK + 1;
 template <int DT>
 __device__ __forceinline__ void pack_brick(const VolumeDesc &V, int b, int bx, int by, int bz, int l)
 {
     using S = typename Storage<DT>::T;
-    const int x = bx * BRICK + (l & 7), y = by * BRICK + ((l >> 3) & 7), z = bz * BRICK + (l >> 6);
+    __shared__ S tile[HALO * HALO * HALO];  // [z][y][x]
+    const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
     const S *vals = reinterpret_cast<const S *>(V.values);
-    S c[8];
-    for (int k = 0; k < 8; ++k) {
-        const int xx = min(x + (k & 1), V.dim[0] - 1), yy = min(y + ((k >> 1) & 1), V.dim[1] - 1),
-                  zz = min(z + (k >> 2), V.dim[2] - 1);
-        c[k] = vals[brick_index(V, xx, yy, zz)];
+    tile[(lz * HALO + ly) * HALO + lx] = vals[(size_t)b * BRICK_VOX + l];
+    if (l < 217) {
+        int hx, hy, hz;
+        if (l < 64) {
+            hx = 8, hy = l & 7, hz = l >> 3;
+        } else if (l < 128) {
+            hx = l & 7, hy = 8, hz = (l - 64) >> 3;
+        } else if (l < 192) {
+            hx = l & 7, hy = (l - 128) >> 3, hz = 8;
+        } else if (l < 200) {
+            hx = 8, hy = 8, hz = l - 192;
+        } else if (l < 208) {
+            hx = 8, hy = l - 200, hz = 8;
+        } else if (l < 216) {
+            hx = l - 208, hy = 8, hz = 8;
+        } else {
+            hx = 8, hy = 8, hz = 8;
+        }
+        const int xx = min(bx * BRICK + hx, V.dim[0] - 1), yy = min(by * BRICK + hy, V.dim[1] - 1),
+                  zz = min(bz * BRICK + hz, V.dim[2] - 1);
+        tile[(hz * HALO + hy) * HALO + hx] = vals[brick_index(V, xx, yy, zz)];
     }
+    __syncthreads();
+    // (in the last brick along an axis the face holds the clamped voxel, the
+    // brick's own last layer, so cells on the volume's upper faces need no test)
+    S c[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        c[k] = tile[((lz + (k >> 2)) * HALO + ly + ((k >> 1) & 1)) * HALO + lx + (k & 1)];
     const size_t rec = (size_t)b * BRICK_VOX + l;
     bool all_free = true, any_unobserved = false;
     if (DT == RF_F32) {
@@ -305,55 +350,32 @@ __device__ __forceinline__ void pack_brick(const VolumeDesc &V, int b, int bx, i
 }
 
 
-// Packed cells of the bricks whose values may have changed: brick B needs
-// repacking when any of the bricks B + {0,1}^3 is dirty (or `all`).  Each CTA
-// walks FUSE_BRICKS_PER_CTA consecutive bricks; thread 0 reads the dirty flags
-// and the CTA skips bricks that need nothing.
+// Packed cells of the bricks on the repack list, or of every brick (`all`, after
+// an upload or a reset).  A persistent grid walks the list, one brick per CTA step.
 template <int DT>
 __global__ void __launch_bounds__(512) pack_cells_kernel(VolumeDesc V, int all, int nbricks)
 {
-    // warp 0 reads the 8 x 8 dirty flags of this CTA's bricks in parallel (lane
-    // i: brick i / 8 and i / 8 + 4, neighbour i % 8); one barrier publishes the mask
-    __shared__ unsigned s_need;
     const int l = threadIdx.x;
-    if (l < 32) {
-        unsigned bits = 0u;
-        for (int half = 0; half < 2; ++half) {
-            const int j = (l >> 3) + 4 * half, c = l & 7;
-            const int b = blockIdx.x * FUSE_BRICKS_PER_CTA + j;
-            bool d = false;
-            if (b < nbricks) {
-                const int bx = b % V.nb[0], by = (b / V.nb[0]) % V.nb[1], bz = b / (V.nb[0] * V.nb[1]);
-                const int nx = bx + (c & 1), ny = by + ((c >> 1) & 1), nz = bz + (c >> 2);
-                d = all != 0 || (nx < V.nb[0] && ny < V.nb[1] && nz < V.nb[2] &&
-                                 V.dirty[nx + V.nb[0] * (ny + V.nb[1] * nz)] != 0);
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, d);  // bit 8 q + c: brick q (+ 4 half)
-            for (int q = 0; q < 4; ++q)
-                if ((m >> (8 * q)) & 0xffu)
-                    bits |= 1u << (q + 4 * half);
-        }
-        if (l == 0)
-            s_need = bits;
-    }
-    __syncthreads();
-    const unsigned need = s_need;
-    for (int j = 0; j < FUSE_BRICKS_PER_CTA; ++j) {
-        if (!((need >> j) & 1u))
-            continue;  // uniform across the CTA (also every brick past the end)
-        const int b = blockIdx.x * FUSE_BRICKS_PER_CTA + j;
+    const int n = all ? nbricks : (int)V.fuse_count[1];
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const int b = all ? i : V.fuse_list[nbricks + i];
         pack_brick<DT>(V, b, b % V.nb[0], (b / V.nb[0]) % V.nb[1], b / (V.nb[0] * V.nb[1]), l);
         if (l == 0)
             atomicAdd(&V.counters[2], 1ull);
     }
 }
 
-// Rebuild the packed cells after the values changed (all = every brick, else
-// the dirty ones), then clear the dirty flags.  Stream-ordered, capturable.
+// Bytes of the fusion bookkeeping cleared before each fusion: the two list
+// counts (padded to 16 B) and the repack bit set.
+static size_t fuse_flags_bytes(int nbricks) { return 16 + (size_t)((nbricks + 31) / 32) * 4; }
+
+// Rebuild the packed cells after the values changed: every brick (all), else
+// the repack list of the fusion that ran last on the stream.  Stream-ordered,
+// capturable.
 rf_status pack_cells(const VolumeDesc &V, int all, cudaStream_t s)
 {
     const int nbricks = V.nb[0] * V.nb[1] * V.nb[2];
-    const int grid = (nbricks + FUSE_BRICKS_PER_CTA - 1) / FUSE_BRICKS_PER_CTA;
+    const int grid = V.fuse_grid[1];
     switch (V.dtype) {
     case RF_F32:
         pack_cells_kernel<RF_F32><<<grid, 512, 0, s>>>(V, all, nbricks);
@@ -366,28 +388,60 @@ rf_status pack_cells(const VolumeDesc &V, int all, cudaStream_t s)
         break;
     }
     RF_CUDA(cudaGetLastError());
-    RF_CUDA(cudaMemsetAsync(V.dirty, 0, (size_t)nbricks, s));
     return RF_OK;
 }
 
+// One fusion: clear the lists, cull, update the visible bricks, repack the
+// bricks that read a changed value.  Four stream-ordered operations, no host
+// synchronisation (capturable).
 static rf_status integrate_any(const VolumeDesc &V, const float *depth, const Intr &K, const Pose &T,
                                const float *pose_dev, const int *status_dev, cudaStream_t s)
 {
     const int nbricks = V.nb[0] * V.nb[1] * V.nb[2];
-    const int grid = (nbricks + FUSE_BRICKS_PER_CTA - 1) / FUSE_BRICKS_PER_CTA;
+    RF_CUDA(cudaMemsetAsync(V.fuse_count, 0, fuse_flags_bytes(nbricks), s));
+    cull_bricks_kernel<<<(nbricks + 255) / 256, 256, 0, s>>>(V, K, T, pose_dev, status_dev, nbricks);
+    RF_CUDA(cudaGetLastError());
+    const int grid = V.fuse_grid[0];
     switch (V.dtype) {
     case RF_F32:
-        integrate_kernel<RF_F32><<<grid, 512, 0, s>>>(V, depth, K, T, pose_dev, status_dev, 255, nbricks);
+        integrate_kernel<RF_F32><<<grid, 512, 0, s>>>(V, depth, K, T, pose_dev, 255, nbricks);
         break;
     case RF_F16:
-        integrate_kernel<RF_F16><<<grid, 512, 0, s>>>(V, depth, K, T, pose_dev, status_dev, 255, nbricks);
+        integrate_kernel<RF_F16><<<grid, 512, 0, s>>>(V, depth, K, T, pose_dev, 255, nbricks);
         break;
     default:
-        integrate_kernel<RF_I16><<<grid, 512, 0, s>>>(V, depth, K, T, pose_dev, status_dev, 255, nbricks);
+        integrate_kernel<RF_I16><<<grid, 512, 0, s>>>(V, depth, K, T, pose_dev, 255, nbricks);
         break;
     }
     RF_CUDA(cudaGetLastError());
     return pack_cells(V, 0, s);
+}
+
+// Persistent grids of the fusion kernels for this device and dtype: the CTAs
+// that fit at once (512 threads each), at most one per brick.
+static rf_status fuse_grids(VolumeDesc &d)
+{
+    int dev = 0, sms = 0, oi = 0, op = 0;
+    RF_CUDA(cudaGetDevice(&dev));
+    RF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    switch (d.dtype) {
+    case RF_F32:
+        RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oi, integrate_kernel<RF_F32>, 512, 0));
+        RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, pack_cells_kernel<RF_F32>, 512, 0));
+        break;
+    case RF_F16:
+        RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oi, integrate_kernel<RF_F16>, 512, 0));
+        RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, pack_cells_kernel<RF_F16>, 512, 0));
+        break;
+    default:
+        RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oi, integrate_kernel<RF_I16>, 512, 0));
+        RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, pack_cells_kernel<RF_I16>, 512, 0));
+        break;
+    }
+    const int nbricks = d.nb[0] * d.nb[1] * d.nb[2];
+    d.fuse_grid[0] = std::max(1, std::min(std::max(oi, 1) * sms, nbricks));
+    d.fuse_grid[1] = std::max(1, std::min(std::max(op, 1) * sms, nbricks));
+    return RF_OK;
 }
 
 rf_status launch_integrate(const VolumeDesc &V, const float *depth, const Intr &K, const Pose &T, cudaStream_t s)
@@ -459,8 +513,13 @@ rf_status rf_volume_create(int dx, int dy, int dz, float voxel, float trunc, con
         e = cudaMalloc(&d.weights, v->n_vox);
     if (e == cudaSuccess)
         e = cudaMalloc(&d.cells, v->n_vox * 8 * dtype_size(dtype));
+    const int nbricks = (int)(v->n_vox / BRICK_VOX);
     if (e == cudaSuccess)
-        e = cudaMalloc(&d.dirty, v->n_vox / BRICK_VOX);
+        e = cudaMalloc(&d.fuse_count, fuse_flags_bytes(nbricks));
+    if (e == cudaSuccess) {
+        d.need = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(d.fuse_count) + 16);
+        e = cudaMalloc(&d.fuse_list, 2 * (size_t)nbricks * sizeof(int));
+    }
     if (e == cudaSuccess)
         e = cudaMalloc(&d.brick_class, v->n_vox / BRICK_VOX);
     if (e == cudaSuccess)
@@ -471,13 +530,16 @@ rf_status rf_volume_create(int dx, int dy, int dz, float voxel, float trunc, con
         cudaFree(d.values);
         cudaFree(d.weights);
         cudaFree(d.cells);
-        cudaFree(d.dirty);
+        cudaFree(d.fuse_count);
+        cudaFree(d.fuse_list);
         cudaFree(d.brick_class);
         cudaFree(d.counters);
         delete v;
         return cuda_fail(e, "cudaMalloc(volume)");
     }
-    rf_status st = rf_volume_reset(v, nullptr);
+    rf_status st = fuse_grids(d);
+    if (st == RF_OK)
+        st = rf_volume_reset(v, nullptr);
     if (st != RF_OK) {
         rf_volume_destroy(v);
         return st;
@@ -494,7 +556,8 @@ void rf_volume_destroy(rf_volume v)
     cudaFree(v->d.values);
     cudaFree(v->d.weights);
     cudaFree(v->d.cells);
-    cudaFree(v->d.dirty);
+    cudaFree(v->d.fuse_count);
+    cudaFree(v->d.fuse_list);
     cudaFree(v->d.brick_class);
     cudaFree(v->d.counters);
     cudaFree(v->scratch);
@@ -523,10 +586,10 @@ rf_status rf_volume_reset(rf_volume v, void *stream)
                                                          v->n_vox);
     RF_CUDA(cudaGetLastError());
     // every packed cell becomes 8 sentinel corners (biased 0 for int16), every
-    // brick is classed invalid, nothing is dirty
+    // brick is classed invalid
     const uint32_t cell_pattern = v->d.dtype == RF_I16 ? 0u : pattern;
     reset_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>((uint32_t *)v->d.cells, 8 * words, cell_pattern,
-                                                         v->d.dirty, v->n_vox / BRICK_VOX);
+                                                         nullptr, 0);
     RF_CUDA(cudaGetLastError());
     RF_CUDA(cudaMemsetAsync(v->d.brick_class, CELLS_INVALID, v->n_vox / BRICK_VOX, (cudaStream_t)stream));
     return RF_OK;

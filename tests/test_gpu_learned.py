@@ -185,11 +185,57 @@ def test_fallback_rule_and_graph_replay(nat, tiny):
     for s in stats[1:]:
         assert s["used_fallback"] == 1 and s["iters_fallback"] >= 1
         assert s["rho_prev"] > 0
-        assert s["chose_fallback"] == int(s["rho_fallback"] > s["rho_learned"])
+        assert s["chose_fallback"] == int(s["rho_fallback"] >= s["rho_learned"])  # a tie goes to the restart
         assert s["lookups"] > 0
     # graph replay gives the same frames bit for bit
     np.testing.assert_array_equal(runs[True][0], poses)
     assert [s["chose_fallback"] for s in runs[True][1]] == [s["chose_fallback"] for s in stats]
+
+
+def test_off_map_proposal_restarts_plain(nat, tiny):
+    """A proposal far outside the volume: the learned run's first iteration finds
+    no TSDF sample for any particle (Sec. 4's first corner case, rho_tilde = 0.5),
+    so the frame restarts plain PFO from s*_{t-1} with the carried r_1 even with
+    theta = 0, and that run is kept; it equals the explicit extended-frame call."""
+    import torch
+
+    cfg, K, traj = tiny["cfg"], tiny["K"], tiny["traj"]
+    n, k_fb = cfg["n_particles"], 20
+    prev = pose_f32(traj[0])
+    r_carry = [0.05] * 6
+    d0, d1 = (torch.from_numpy(tiny["depths"][f]).cuda() for f in (0, 1))
+    params = nat.make_params(k_max=20, stride=cfg["stride"])
+    theta = zero_network_params(np.log(0.3))
+    mlp.unflatten(theta)[7][3] = 100.0  # mu_x = 100 units (10 m): c_0 beyond the 2.56 m volume
+    net = nat.MLP(16)
+    net.set_params(theta)
+
+    gv = gpu_volume(nat, tiny)
+    tr = nat.Tracker(gv, nat.pst_create(n, seed=1), params, cfg["width"], cfg["height"])
+    tr.set_scale(r_carry)
+    lp = nat.Learned(tr, gv, net, nat.proposal_params(k_learned=3, k_fallback=k_fb, theta=0.0), cfg["width"],
+                     cfg["height"])
+    lp.start(tiny["depths"][0], K, prev)
+    sb = nat.new_learned_stats_buffer()
+    pose, status = lp.step(tiny["depths"][1], K, stats_dev=sb)
+    s = nat.learned_stats_dict(sb)
+    assert status == 0 and s["status"] == 0
+    assert abs(s["init_pose"][4] - (prev[4] + 10.0)) < 1e-3
+    assert s["iters_learned"] >= 1 and s["rho_learned"] == 0.5
+    assert s["used_fallback"] == 1 and s["chose_fallback"] == 1 and s["iters_fallback"] >= 1
+
+    gv2 = gpu_volume(nat, tiny)
+    nat.tsdf_integrate(gv2, d0, K, prev)
+    tr2 = nat.Tracker(gv2, nat.pst_create(n, seed=1), params, cfg["width"], cfg["height"])
+    prev_dev = torch.tensor(prev, dtype=torch.float32, device="cuda")
+    pose_f = torch.zeros(7, dtype=torch.float32, device="cuda")
+    st_f = nat.new_stats_buffer()
+    nat.pfo_track_frame_ex_async(tr2, d1, d0, K, prev_dev, pose_f, st_f, init_pose_dev=prev_dev.clone(),
+                                 scale_dev=torch.tensor(r_carry, dtype=torch.float32, device="cuda"), k_max=k_fb)
+    sf = nat.stats_dict(nat.stats_from_device(st_f))
+    assert s["iters_fallback"] == sf["iters"] and s["rho_fallback"] == sf["it"][-1]["rho_tilde"] > 0.5
+    np.testing.assert_array_equal(np.asarray(pose, dtype=np.float32), pose_f.cpu().numpy())
+    assert np.linalg.norm(np.asarray(pose[4:]) - traj[1][4:]) < 0.2  # back on the map, not 10 m away
 
 
 def test_resume_continues_the_learned_run(nat, tiny):

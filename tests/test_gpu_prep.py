@@ -141,6 +141,49 @@ def test_integrate_parity_sequence(oracle, nat, dtype):
         assert np.mean(np.abs(Fg[both] - ov.F[both]) < 0.5 / 32767 + 1e-9) > 0.98
 
 
+def test_integrate_parity_many_bricks(oracle, nat):
+    """A 256^3 int16 volume (32,768 bricks) whose visible bricks outnumber the
+    persistent fusion grid, so every CTA walks several list entries; values and
+    weights match the oracle, and the fusion counters agree with the result:
+    on a fresh volume every updated voxel ends with weight 1, and the bricks that
+    passed the frustum test include every brick holding an updated voxel."""
+    import torch
+
+    dims, voxel, trunc = 256, 0.02, 0.06
+    scene = synth.make_scene(dims * voxel, 0.3, 5)
+    traj = synth.make_trajectory(scene, 3, 3.0, 3.0, 5)
+    K = synth.intrinsics(160, 120)
+    gv = nat.Volume(dims, voxel, trunc, (0, 0, 0), "i16")
+    ov = oracle.Volume((dims,) * 3, voxel, (0, 0, 0), trunc, qmode="i16")
+    amb = np.zeros(dims ** 3, bool)
+    rng = np.random.default_rng(7)
+    for f in range(3):
+        depth = synth.render_depth(scene, traj[f], K, rng)
+        pose = traj[f].astype(np.float32).astype(np.float64)
+        amb |= ov.integrate_ambiguity(depth, K, pose, tol=1e-4).astype(bool)
+        ov.integrate(depth, K, pose, threads=8)
+        gv.counters(reset=True)
+        nat.tsdf_integrate(gv, torch.from_numpy(depth).cuda(), K, pose)
+        c = gv.counters(reset=True)
+        if f == 0:
+            _, W0 = gv.download()
+            w = W0.reshape(dims // 8, 8, dims // 8, 8, dims // 8, 8)
+            bricks_touched = int((w.max(axis=(1, 3, 5)) > 0).sum())
+            assert c["voxels_updated"] == int((W0 > 0).sum())
+            assert bricks_touched <= c["bricks_visited"] < (dims // 8) ** 3
+            assert c["bricks_visited"] > 2 * 152 * 4  # more list entries than CTAs in the grid
+            assert 0 < c["bricks_repacked"] <= 8 * bricks_touched
+    codes, W = gv.download()
+    Fg = synth.decode_values(codes).reshape(-1)
+    Wg = W.reshape(-1).astype(np.int32)
+    sure = ~amb
+    assert sure.mean() > 0.99
+    np.testing.assert_array_equal(Wg[sure], ov.W[sure])
+    assert np.array_equal(np.isfinite(Fg[sure]), np.isfinite(ov.F[sure]))
+    both = sure & np.isfinite(Fg) & np.isfinite(ov.F)
+    np.testing.assert_allclose(Fg[both], ov.F[both], atol=4.0 / 32767)
+
+
 def test_dirty_brick_repacking_matches_full_pack(nat):
     """Fusion repacks only the trilinear cells of bricks it touched; a volume that
     receives the same values by upload (full repack) must score identically."""

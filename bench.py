@@ -61,6 +61,8 @@ def parse():
                     help="frames per sequence (plain configs: the tracked sequence; learned: each held-out one)")
     ap.add_argument("--speed", type=float, default=None, help="learned / ablation config: linear speed (m/s)")
     ap.add_argument("--ang-speed", type=float, default=None, help="learned / ablation config: angular speed (rad/s)")
+    ap.add_argument("--test-speeds", default=None,
+                    help="learned config: extra held-out speed pairs 'm/s:rad/s,...' evaluated with the trained network")
     ap.add_argument("--labels", choices=["tracked", "truth"], default="truth",
                     help="learned config: label frames tracked along the sequence at 60 Hz, or from the true "
                          "previous pose at 30 Hz")
@@ -822,6 +824,26 @@ def run_learned_bench(args):
                       "unstuck": sum(r["unstuck"] for r in rows_i),
                       "iters_per_frame": float(np.mean([r["learned_iters"] for r in rows_i]))})
     params = nat.proposal_params(**dict(dict(k_learned=spec["k_learned"]), **settings[0]))
+    # the same network and default setting on held-out sequences at other speeds
+    other_speeds = []
+    for item in (args.test_speeds or "").split(","):
+        if not item.strip():
+            continue
+        sp, asp = (float(x) for x in item.split(":"))
+        spec_o = dict(spec, speed=sp, ang_speed=asp)
+        rows_o = learned.evaluate(nat, spec_o, seeds_te, frames, net, params, use_graph=True, warmup=W, flush=flush,
+                                  plain=True)
+        nf_o = sum(r["frames"] for r in rows_o)
+        other_speeds.append({
+            "speed": sp, "ang_speed": asp,
+            "plain": {"frames_per_s": nf_o / sum(r["plain_s"] for r in rows_o),
+                      "ate_cm_mean": float(np.mean([r["plain_ate_cm"] for r in rows_o])),
+                      "ate_cm": [round(r["plain_ate_cm"], 2) for r in rows_o]},
+            "learned": {"frames_per_s": nf_o / sum(r["learned_s"] for r in rows_o),
+                        "ate_cm_mean": float(np.mean([r["learned_ate_cm"] for r in rows_o])),
+                        "ate_cm": [round(r["learned_ate_cm"], 2) for r in rows_o],
+                        "restarts": sum(r["fallbacks"] for r in rows_o), "resumes": sum(r["resumed"] for r in rows_o),
+                        "unstuck": sum(r["unstuck"] for r in rows_o)}})
     clk = clocks.stop()
     t_l = sum(r["learned_s"] for r in rows)
     t_p = sum(r["plain_s"] for r in rows)
@@ -878,6 +900,7 @@ def run_learned_bench(args):
         "labels": {"mode": args.labels, "tracked_ate_cm_mean": float(np.mean(label_ate)), "samples": int(len(seq)),
                    "seconds": label_seconds},
         "sweep": sweep,
+        "other_speeds": other_speeds,
         "network": {"train_step_ms": 1e3 * t_train, "forward_b1_ms": 1e3 * t_fwd,
                     "train_tflops": 3 * flops_fwd * 512 / t_train / 1e12,
                     "val_loss": [round(v, 4) for v in hist["val"]],

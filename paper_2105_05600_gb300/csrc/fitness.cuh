@@ -264,14 +264,10 @@ __device__ __forceinline__ int fitness_points_i16_packed(const CellView &V, cons
             const f2_t VV = f2_mul(f2_fma(FZ[p], f2_sub(Y1, Y0), Y0), SCALE);
             float va, vb;
             f2_unpack(VV, va, vb);
-            bool oka = (a.x & 0xFFFFu) != 0u, okb = (b.x & 0xFFFFu) != 0u;
+            const bool oka = (a.x & 0xFFFFu) != 0u, okb = (b.x & 0xFFFFu) != 0u;
+            nv += (oka ? 1 : 0) + (okb ? 1 : 0);
             va = oka ? va : 1.f;
             vb = okb ? vb : 1.f;
-            if (RF_I16_MARKER) {  // free space (as cell_eval)
-                oka = oka || a.x == I16_FREE_MARKER;
-                okb = okb || b.x == I16_FREE_MARKER;
-            }
-            nv += (oka ? 1 : 0) + (okb ? 1 : 0);
             grp += L1 ? fabsf(va) : va * va;
             grp += L1 ? fabsf(vb) : vb * vb;
         }

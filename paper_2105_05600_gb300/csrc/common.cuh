@@ -50,6 +50,7 @@ struct VolumeDesc {
     // passed the frustum test, listed in fuse_list[0, nbricks); fuse_count[1] bricks
     // whose cells are to be repacked, listed in fuse_list[nbricks, 2 nbricks) and
     // marked in the bit set `need` (one bit per brick, so a brick is listed once).
+    // An entry is the brick's coordinates bx | by << 10 | bz << 20.
     // fuse_count and need are one allocation, cleared together before each fusion.
     unsigned *fuse_count;
     uint32_t *need;

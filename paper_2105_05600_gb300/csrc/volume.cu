@@ -153,6 +153,17 @@ __device__ __forceinline__ bool brick_may_update(const VolumeDesc &V, int bx, in
     return true;
 }
 
+// Work-list entries carry brick coordinates, so the fusion kernels index a
+// brick without integer division: bx | by << 10 | bz << 20 (at most 256 bricks
+// per axis).
+__device__ __forceinline__ int brick_code(int bx, int by, int bz) { return bx | (by << 10) | (bz << 20); }
+__device__ __forceinline__ void brick_decode(int e, int &bx, int &by, int &bz)
+{
+    bx = e & 1023;
+    by = (e >> 10) & 1023;
+    bz = e >> 20;
+}
+
 __device__ __forceinline__ void load_pose(Pose &T, const float *pose_dev)
 {
     if (pose_dev) {
@@ -178,8 +189,8 @@ __global__ void __launch_bounds__(256) cull_bricks_kernel(VolumeDesc V, Intr K, 
     float R[9];
     quat_rot(T.q, R);
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool vis = b < nbricks &&
-                     brick_may_update(V, b % V.nb[0], (b / V.nb[0]) % V.nb[1], b / (V.nb[0] * V.nb[1]), R, T.t, K);
+    const int bx = b % V.nb[0], by = (b / V.nb[0]) % V.nb[1], bz = b / (V.nb[0] * V.nb[1]);
+    const bool vis = b < nbricks && brick_may_update(V, bx, by, bz, R, T.t, K);
     const unsigned m = __ballot_sync(0xffffffffu, vis);
     if (m == 0u)
         return;  // warp-uniform
@@ -191,7 +202,7 @@ __global__ void __launch_bounds__(256) cull_bricks_kernel(VolumeDesc V, Intr K, 
     }
     base = __shfl_sync(0xffffffffu, base, 0);
     if (vis)
-        V.fuse_list[base + __popc(m & ((1u << lane) - 1u))] = b;
+        V.fuse_list[base + __popc(m & ((1u << lane) - 1u))] = brick_code(bx, by, bz);
 }
 
 // Projective TSDF fusion (Sec. 3 overview; Curless & Levoy 1996, KinectFusion
@@ -212,8 +223,9 @@ __global__ void __launch_bounds__(512, 4) integrate_kernel(VolumeDesc V, const f
     const int l = threadIdx.x;
     const int n_visible = (int)V.fuse_count[0];
     for (int i = blockIdx.x; i < n_visible; i += gridDim.x) {
-        const int b = V.fuse_list[i];
-        const int bx = b % V.nb[0], by = (b / V.nb[0]) % V.nb[1], bz = b / (V.nb[0] * V.nb[1]);
+        int bx, by, bz;
+        brick_decode(V.fuse_list[i], bx, by, bz);
+        const int b = bx + V.nb[0] * (by + V.nb[1] * bz);
         const int x = bx * BRICK + (l & 7), y = by * BRICK + ((l >> 3) & 7), z = bz * BRICK + (l >> 6);
         bool updated = false, changed = false;
         do {
@@ -262,7 +274,7 @@ __global__ void __launch_bounds__(512, 4) integrate_kernel(VolumeDesc V, const f
                 const int nbk = nx + V.nb[0] * (ny + V.nb[1] * nz);
                 const uint32_t bit = 1u << (nbk & 31);
                 if (!(atomicOr(&V.need[nbk >> 5], bit) & bit))
-                    V.fuse_list[nbricks + (int)atomicAdd(&V.fuse_count[1], 1u)] = nbk;
+                    V.fuse_list[nbricks + (int)atomicAdd(&V.fuse_count[1], 1u)] = brick_code(nx, ny, nz);
             }
         }
         if (l == 0)
@@ -358,8 +370,15 @@ __global__ void __launch_bounds__(512) pack_cells_kernel(VolumeDesc V, int all, 
     const int l = threadIdx.x;
     const int n = all ? nbricks : (int)V.fuse_count[1];
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
-        const int b = all ? i : V.fuse_list[nbricks + i];
-        pack_brick<DT>(V, b, b % V.nb[0], (b / V.nb[0]) % V.nb[1], b / (V.nb[0] * V.nb[1]), l);
+        int bx, by, bz;
+        if (all) {  // uniform: after an upload or a reset only
+            bx = i % V.nb[0];
+            by = (i / V.nb[0]) % V.nb[1];
+            bz = i / (V.nb[0] * V.nb[1]);
+        } else {
+            brick_decode(V.fuse_list[nbricks + i], bx, by, bz);
+        }
+        pack_brick<DT>(V, bx + V.nb[0] * (by + V.nb[1] * bz), bx, by, bz, l);
         if (l == 0)
             atomicAdd(&V.counters[2], 1ull);
     }

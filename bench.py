@@ -61,6 +61,8 @@ def parse():
                     help="frames per sequence (plain configs: the tracked sequence; learned: each held-out one)")
     ap.add_argument("--speed", type=float, default=None, help="learned / ablation config: linear speed (m/s)")
     ap.add_argument("--ang-speed", type=float, default=None, help="learned / ablation config: angular speed (rad/s)")
+    ap.add_argument("--train-speeds", default=None,
+                    help="learned config (--labels truth): training sequences take these 'm/s:rad/s,...' pairs in turn")
     ap.add_argument("--test-speeds", default=None,
                     help="learned config: extra held-out speed pairs 'm/s:rad/s,...' evaluated with the trained network")
     ap.add_argument("--labels", choices=["tracked", "truth"], default="truth",
@@ -765,8 +767,9 @@ def run_learned_bench(args):
     W = max(3, args.warmup)
     seeds_tr = rank_seeds(spec["train_seeds"][:n_train], rank)
     seeds_te = rank_seeds(spec["test_seeds"][args.test_first:args.test_first + n_test], rank)
+    train_speeds = [tuple(float(x) for x in it.split(":")) for it in (args.train_speeds or "").split(",") if it.strip()]
     ds = learned.generate_dataset(nat, spec, seeds_tr, train_frames, substeps=spec["label_substeps"],
-                                  start=args.labels)
+                                  start=args.labels, speeds=train_speeds or None)
     n_val = max(1, n_train // 8)
     seq = ds["seq"]
     tr_rows, va_rows = np.flatnonzero(seq < n_train - n_val), np.flatnonzero(seq >= n_train - n_val)
@@ -884,6 +887,7 @@ def run_learned_bench(args):
         "dtype": "f32 tracking, bf16 x bf16 -> f32 network", "data": "synthetic (seeded rooms and trajectories; "
         "training seeds 100.., held-out seeds 1000.. for the A/B)",
         "config": {"workload": workload, "l2": "flushed before every timed frame (512 MiB write outside the events)",
+                   "train_speeds": train_speeds or [(spec["speed"], spec["ang_speed"])],
                    "train": f"{n_train} sequences x {train_frames} frames (labels: plain PFO, "
                             f"{'from the true previous pose at 30 Hz' if args.labels == 'truth' else 'tracked at 60 Hz'}), "
                             f"{hist['steps']} Adam steps of 512, best epoch {hist.get('best_epoch')}",

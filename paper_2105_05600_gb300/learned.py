@@ -45,7 +45,7 @@ def _tracker(nat, spec, k_max=None, flags=None):
 
 # ----------------------------------------------------------------------------- data
 def generate_dataset(nat, spec: dict, seeds, n_frames: int, substeps: int = 2, group: int = 16,
-                     use_graph: bool = True, start: str = "tracked"):
+                     use_graph: bool = True, start: str = "tracked", speeds=None):
     """Training pairs from the plain tracker (Algorithm 1 with the Sec. 4
     initialisation, fusion of every frame; up to `group` sequences per batched
     step).  The samples are the network input of (D_t, D_{t-1}, s_{t-2},
@@ -65,7 +65,7 @@ def generate_dataset(nat, spec: dict, seeds, n_frames: int, substeps: int = 2, g
     import torch
 
     if start == "truth":
-        return _dataset_from_truth(nat, spec, seeds, n_frames)
+        return _dataset_from_truth(nat, spec, seeds, n_frames, speeds)
     seeds = list(seeds)
     n_rows = len(seeds) * (n_frames - 1)
     X = torch.zeros((n_rows, 832), dtype=torch.bfloat16, device="cuda")
@@ -113,10 +113,12 @@ def generate_dataset(nat, spec: dict, seeds, n_frames: int, substeps: int = 2, g
     return dict(X=X, Y=Y, seq=seq, tracked=tracked, truth=truth, seconds=time.perf_counter() - t0)
 
 
-def _dataset_from_truth(nat, spec, seeds, n_frames):
+def _dataset_from_truth(nat, spec, seeds, n_frames, speeds=None):
     """generate_dataset(start="truth"): per sequence, frame 0 fused at its true
     pose; every frame t tracked by plain PFO from the true pose of frame t-1
-    (with the tracker's carried r_1) and fused at its true pose."""
+    (with the tracker's carried r_1) and fused at its true pose.  speeds: an
+    optional list of (m/s, rad/s) pairs taken in turn by the sequences (default:
+    the spec's speed for all)."""
     import torch
 
     seeds = list(seeds)
@@ -128,7 +130,9 @@ def _dataset_from_truth(nat, spec, seeds, n_frames):
     t0 = time.perf_counter()
     row = 0
     for si, s in enumerate(seeds):
-        _, traj, K, D = make_sequence(spec, s, n_frames)
+        spec_s = spec if not speeds else dict(spec, speed=speeds[si % len(speeds)][0],
+                                                ang_speed=speeds[si % len(speeds)][1])
+        _, traj, K, D = make_sequence(spec_s, s, n_frames)
         vol, pst, tr = _tracker(nat, spec)
         gt = torch.as_tensor(traj, dtype=torch.float32, device="cuda")
         poses = torch.zeros_like(gt)

@@ -59,8 +59,8 @@ def parse():
     ap.add_argument("--test-first", type=int, default=0, help="learned config: index of the first held-out seed")
     ap.add_argument("--frames", type=int, default=None,
                     help="frames per sequence (plain configs: the tracked sequence; learned: each held-out one)")
-    ap.add_argument("--speed", type=float, default=None, help="learned / ablation config: linear speed (m/s)")
-    ap.add_argument("--ang-speed", type=float, default=None, help="learned / ablation config: angular speed (rad/s)")
+    ap.add_argument("--speed", type=float, default=None, help="trajectory linear speed (m/s) instead of the config's")
+    ap.add_argument("--ang-speed", type=float, default=None, help="trajectory angular speed (rad/s) instead of the config's")
     ap.add_argument("--train-speeds", default=None,
                     help="learned config (--labels truth): training sequences take these 'm/s:rad/s,...' pairs in turn")
     ap.add_argument("--test-speeds", default=None,
@@ -1238,6 +1238,10 @@ def main():
             print(json.dumps(res))
         return
     cfg = dict(synth.CONFIGS[args.config])
+    if args.speed is not None:
+        cfg["speed"] = args.speed
+    if args.ang_speed is not None:
+        cfg["ang_speed"] = args.ang_speed
     res = run_reference(args, cfg) if args.impl == "reference" else run_ours(args, cfg)
     if res is not None:
         print(json.dumps(res))
